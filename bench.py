@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 DFTT noisy-statevector engine.
+
+Workload (default): the 28-qubit QAOA-style circuit on a seeded random
+3-regular graph, 4 layers of RZZ(gamma) + RX(beta), 2q depolarizing 5e-3
+and 1q 5e-4, 1e6 shots, alpha = 0.01, beta = 100, complex64 state (2 GiB)
+with an FP64 output distribution (2 GiB).
+
+A step is one traversal of the whole instance tree on the device: every
+fused pass, Pauli injection, leaf accumulation, drift check and snapshot
+restore (the plan -- ER sampling, tally, commutation, pruning, DFS order --
+is built and its device program uploaded before the timed region; the
+end-to-end number below includes them).  ``value`` = kept instances
+(leaves) per second over all ranks.
+
+Also reported: gate-amplitude updates/s (executed, and the from-scratch
+equivalent N_l * G * 2^n), the HBM roofline of the fused pass kernel
+measured live with CUDA events around each pass launch, the end-to-end
+rate through the C ABI from host buffers (plan + compile + upload +
+traversal + copy of the distribution back), the oracle on the host cores
+as the CPU baseline, and SM clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the reference arm): each step
+simulates a bounded prefix of the first instance of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import tusq_workloads as W  # noqa: E402
+
+WORKLOAD_DESC = {
+    "qaoa_28q": "28-qubit QAOA on a seeded random 3-regular graph, p=4 layers RZZ(gamma)+RX(beta), "
+                "2q depolarizing 5e-3, 1q 5e-4, 1e6 shots, alpha=0.01 beta=100",
+    "brickwork_20q": "20-qubit brickwork depth 40, Haar SU(2) + CZ, depolarizing 1e-3/1e-2, 1e6 shots",
+    "random_layers_6q": "6-qubit random layers depth 20, depolarizing 1e-3/1e-2, 1e4 shots",
+}
+SHOTS = {"qaoa_28q": 1_000_000, "brickwork_20q": 1_000_000, "random_layers_6q": 10_000}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_src: str):
+    """Per-launch DRAM traffic of the pass kernel from the committed ncu
+    summary, scaled to bytes per algorithmic byte; None when the kernel
+    source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    fields = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernels_cu_sha256_16") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_algorithmic_byte"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(circ, plan_inst, budget_s: float = 15.0):
+    """The oracle as it stands, timed on a bounded sample: a prefix of the
+    first kept instance's gates (with its Pauli events), sized to about
+    budget_s of host work; the rate is scaled to instances/s."""
+    import oracle
+    G = circ.n_gates
+    ev = list(plan_inst[0])
+    k = 2
+    while True:
+        sub = W.Circuit(circ.n_qubits, circ.gates[:k], circ.channels[:k])
+        t0 = time.perf_counter()
+        oracle.simulate(sub, [e for e in ev if e[0] < k])
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or k >= G:
+            break
+        k = min(G, max(k + 1, int(k * min(8.0, budget_s / max(dt, 1e-3)))))
+    rate = (k / G) / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": rate, "unit": "instances/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {k} of {G} gates of one instance ({circ.n_qubits} qubits, complex128), "
+                      f"{dt:.2f} s, scaled by {G}/{k}"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on bounded samples of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    circ = W.WORKLOADS[args.workload]()
+    G = circ.n_gates
+    k = max(1, min(G, args.ref_gates))
+    sub = W.Circuit(circ.n_qubits, circ.gates[:k], circ.channels[:k])
+    for _ in range(args.warmup):
+        oracle.simulate(sub, [])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.simulate(sub, [])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (k / G) / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": "noisy instances/s", "value": value, "unit": "instances/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC[args.workload], "sample_gates": k},
+        "cpu_baseline": {"value": value, "unit": "instances/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {k} of {G} gates of one instance, scaled by {G}/{k}"},
+        "e2e": {"value": value, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qaoa_28q", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--traversal", default="snapshot", choices=["dftt", "scratch", "snapshot"])
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--ref-gates", type=int, default=12)
+    ap.add_argument("--compare", action="store_true", help="also time the other traversals")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2508_04880_b300 as T
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    trav = {"dftt": T.DFTT, "scratch": T.FROM_SCRATCH, "snapshot": T.DFTT_SNAPSHOT}[args.traversal]
+    prec = T.C64 if args.precision == "c64" else T.C128
+    circ = W.WORKLOADS[args.workload]()
+    shots = SHOTS[args.workload]
+    seed = rank     # weak scaling: every rank simulates its own noisy job
+    t0 = time.perf_counter()
+    plan = T.plan(circ, shots, seed)
+    plan_s = time.perf_counter() - t0
+    pst = plan.stats()
+    n = circ.n_qubits
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    opts = T.run_opts(precision=prec, traversal=trav)
+    ex = T.Exec(plan, opts, sp)
+    probs = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ex.launch(probs.data_ptr(), sp)
+    info = ex.finish()
+
+    # timed region: K traversals back to back on the stream; the state and
+    # output (2 GiB each at 28 qubits) exceed the 126 MB L2
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ex.launch(probs.data_ptr(), sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    info = ex.finish()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_inst = pst["n_instances"]
+    secs = ms / 1e3
+    value = n_inst * world / secs
+    amps = float(1 << n)
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+
+    # live roofline of the pass kernel: events around every pass launch
+    ex.set_profiling(True)
+    ex.launch(probs.data_ptr(), sp)
+    ex.finish()
+    pms, pbytes = ex.pass_profile()
+    ex.set_profiling(False)
+    achieved = float(pbytes.sum() / (pms.sum() / 1e3) / 1e9) if len(pms) else 0.0
+    ratio = traffic_from_profile(os.path.join(ROOT, "paper_2508_04880_b300", "csrc", "kernels.cu"))
+    per_launch_bytes = float(pbytes.mean()) if len(pbytes) else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": (ratio * per_launch_bytes) if ratio else None,
+                "kernel": "pass_kernel<float,5>", "launches_per_step": int(len(pms)),
+                "mean_launch_ms": float(pms.mean()) if len(pms) else 0.0,
+                "algorithmic_bytes_per_launch": per_launch_bytes}
+
+    # end to end through the C ABI from host buffers: plan (host ECM),
+    # compile + upload of the device program, traversal, copy of the
+    # distribution to pinned host memory
+    host_out = torch.empty(1 << n, dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    h2d = 0
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl2 = T.plan(circ, shots, seed)
+        ex2 = T.Exec(pl2, opts, sp)
+        ex2.launch(probs.data_ptr(), sp)
+        host_out.copy_(probs, non_blocking=True)
+        info2 = ex2.finish()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d = int(info2["program_bytes"])
+        del ex2
+    e2e_s = min(e2e_times)
+    total = float(host_out.sum())
+
+    line = {
+        "metric": "noisy instances/s", "value": value, "unit": "instances/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "qubits": n, "gates": circ.n_gates,
+                   "shots": shots, "instances": n_inst, "traversal": args.traversal,
+                   "l2": "inputs larger than L2 (state and output 2^n x 8 B each)",
+                   "parallelism": f"replica x{world}"},
+        "gate_amp_updates_per_s": (info["gate_apps"] + info["pauli_apps"]) * amps * world / secs,
+        "scratch_equiv_gate_amp_updates_per_s": pst["scratch_gate_apps"] * amps * world / secs,
+        "hbm_fraction_whole_step": info["algorithmic_bytes"] / secs / 1e9 / hbm_peak,
+        "roofline": roofline,
+        "e2e": {"value": n_inst * world / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(8 * (1 << n)), "seconds": e2e_s, "plan_seconds": plan_s,
+                "sum_probs": total},
+        "gpu_launches": int(info["kernel_launches"]) * args.steps,
+        "run_info": {k: info[k] for k in ("passes", "gate_apps", "pauli_apps", "leaf_passes", "checks",
+                                          "restores", "unrecovered", "resets", "max_drift")},
+        "plan": {k: pst[k] for k in ("n_raw_unique", "n_commuted_unique", "n_instances",
+                                     "dftt_gate_apps", "scratch_gate_apps")},
+        "clocks": clk.summary(),
+    }
+    if args.compare and rank == 0:
+        other = {}
+        for name, tv in (("dftt", T.DFTT), ("scratch", T.FROM_SCRATCH), ("snapshot", T.DFTT_SNAPSHOT)):
+            e3 = T.Exec(plan, T.run_opts(precision=prec, traversal=tv), sp)
+            e3.launch(probs.data_ptr(), sp)
+            e3.finish()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e3.launch(probs.data_ptr(), sp)
+            b.record(stream)
+            inf3 = e3.finish()
+            other[name] = {"ms": a.elapsed_time(b), "passes": inf3["passes"],
+                           "instances_per_s": n_inst / (a.elapsed_time(b) / 1e3)}
+            del e3
+        line["traversals"] = other
+    if rank == 0 and not args.no_cpu_baseline:
+        inst = plan.instances()[0]
+        line["cpu_baseline"] = cpu_baseline(circ, inst)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,286 @@
+/*
+ * tusq.h -- C ABI of the B300 DFTT noisy-statevector engine.
+ *
+ * The engine implements the hot path of TUSQ (arXiv 2508.04880): the Error
+ * Characterization Module (ER sampling and tallying, ER commutation,
+ * pruning; Sec. III-A) on the host, and Depth-First Tree Traversal (DFTT,
+ * Sec. III-B) of the resulting instance tree on one GPU, accumulating the
+ * tally-weighted output distribution.
+ *
+ * Conventions shared with callers:
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - gate kinds: see enum tusq_gate_kind; RX/RY/RZ(t) = exp(-i t sigma/2),
+ *     RZZ(t) = exp(-i t Z(x)Z/2); two-qubit gates on (q0, q1) use the local
+ *     basis index 2*bit(q0) + bit(q1); CX has control q0, target q1;
+ *   - Pauli codes: I=0 X=1 Y=2 Z=3; a two-qubit Pauli is 4*P(q0) + P(q1).
+ *
+ * Errors: every function returning int returns TUSQ_OK (0) or a negative
+ * status; tusq_last_error() gives a thread-local message for the last
+ * failure on the calling thread.  No function aborts the process.
+ * Thread safety: distinct objects may be used from distinct threads; one
+ * object must not be used concurrently.
+ */
+#ifndef TUSQ_ABI_H_INCLUDED
+#define TUSQ_ABI_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUSQ_OK            0
+#define TUSQ_EINVAL       -1  /* bad argument (size, index, kind, probability) */
+#define TUSQ_ENOMEM       -2  /* host or device allocation failed */
+#define TUSQ_ENOMEM_ADMIT -3  /* serving: job footprint exceeds the HBM budget */
+#define TUSQ_ECUDA        -4  /* a CUDA runtime call failed */
+#define TUSQ_EDRIFT       -5  /* drift above tolerance at a node without a snapshot */
+#define TUSQ_ETIMEOUT     -6  /* a bounded device wait ran out */
+#define TUSQ_EBUSY        -7  /* object in use / job not finished */
+#define TUSQ_ENOTFOUND    -8  /* unknown job id */
+
+enum tusq_gate_kind {
+    TUSQ_H = 0, TUSQ_X, TUSQ_Y, TUSQ_Z, TUSQ_S, TUSQ_SDG, TUSQ_T, TUSQ_TDG,
+    TUSQ_RX, TUSQ_RY, TUSQ_RZ, TUSQ_U1Q, TUSQ_CX, TUSQ_CZ, TUSQ_RZZ, TUSQ_U2Q
+};
+
+enum tusq_precision { TUSQ_C64 = 0, TUSQ_C128 = 1 };
+
+/* Commutation rule sets (Sec. III-A3).  PAPER: rules 1-6 -- Pauli gates,
+ * same-axis rotations RX/RY/RZ, CX.  CLIFFORD (default): additionally H, S,
+ * SDG, CZ by conjugation and T, TDG, RZZ for Paulis that commute with them.
+ * Every rule is exact up to a global phase, so the output is unchanged. */
+enum tusq_commute_mode { TUSQ_COMMUTE_OFF = 0, TUSQ_COMMUTE_PAPER = 1, TUSQ_COMMUTE_CLIFFORD = 2 };
+
+enum tusq_traversal {
+    TUSQ_DFTT = 0,          /* uncompute back to each branch point (Sec. III-B) */
+    TUSQ_FROM_SCRATCH = 1,  /* every instance from |0..0> (the plain form) */
+    TUSQ_DFTT_SNAPSHOT = 2  /* DFTT that restores a branch node from its LIFO
+                               snapshot when it has one (one copy pass instead of
+                               uncomputing), uncomputing otherwise */
+};
+
+typedef struct tusq_circuit tusq_circuit;   /* opaque, library-owned */
+typedef struct tusq_plan_t tusq_plan_t;     /* opaque, immutable after tusq_plan */
+typedef struct tusq_exec tusq_exec;         /* opaque device program + buffers */
+typedef struct tusq_server tusq_server;     /* opaque serving loop */
+
+/* ------------------------------------------------------------- circuits */
+
+/* New empty circuit on n_qubits (1..34).  *out is owned by the caller and
+ * released with tusq_circuit_free. */
+int tusq_circuit_create(int n_qubits, tusq_circuit **out);
+
+/* Append gate `kind` on q0 (and q1 for two-qubit kinds; pass -1 otherwise).
+ * params: RX/RY/RZ/RZZ take 1 angle; U1Q takes a row-major 2x2 complex
+ * matrix as 8 doubles (re, im pairs); U2Q a 4x4 one as 32 doubles; other
+ * kinds take none.  The matrix of U1Q/U2Q must be unitary (checked to 1e-9).
+ * Returns the gate index through the return value when >= 0. */
+int tusq_circuit_add_gate(tusq_circuit *c, int kind, int q0, int q1,
+                          const double *params, int n_params);
+
+/* Attach a Pauli channel right after gate gate_index, acting on that gate's
+ * qubits (Sec. II: noise as a classical mixture of Pauli circuits).
+ * pauli_codes[n_terms] are the non-identity outcomes (1..3 for a one-qubit
+ * gate, 1..15 for a two-qubit gate), probs[n_terms] their probabilities; the
+ * identity gets 1 - sum(probs), which must be >= 0.  n_terms <= 15. */
+int tusq_circuit_set_channel(tusq_circuit *c, int gate_index, int n_terms,
+                             const uint8_t *pauli_codes, const double *probs);
+
+void tusq_circuit_free(tusq_circuit *c);
+
+/* ---------------------------------------------------------------- plans */
+
+typedef struct {
+    double alpha;       /* significance threshold, Sec. III-A4 (paper: 0.01) */
+    uint32_t beta;      /* insignificant instances kept, Sec. III-A4 (paper: 100) */
+    int prune;          /* 0: keep every distinct instance with weight c/S */
+    int commute_mode;   /* enum tusq_commute_mode */
+    int n_threads;      /* host threads for sampling/commutation; 0 = all cores */
+} tusq_plan_opts;
+
+typedef struct {
+    uint64_t shots;               /* S */
+    uint64_t n_channels;          /* C */
+    uint64_t n_gates;             /* G = tree height in gate slots */
+    uint64_t n_raw_unique;        /* distinct ERs after tallying (Sec. III-A1) */
+    uint64_t n_commuted_unique;   /* distinct instances after commutation (III-A2) */
+    uint64_t n_significant;       /* |C_S| */
+    uint64_t n_insignificant;     /* |C_I| */
+    uint64_t n_picked;            /* min(beta, |C_I|) */
+    uint64_t n_instances;         /* leaves N_l = S_final (Eq. S_final) */
+    uint64_t tree_gate_edges;     /* |E| counted in gate applications */
+    uint64_t dftt_gate_apps;      /* 2|E| - G: DFTT without root resets */
+    uint64_t scratch_gate_apps;   /* N_l * G: every instance from scratch */
+    uint64_t dftt_pauli_apps;     /* Pauli applications of the same traversal */
+    uint64_t scratch_pauli_apps;
+    double seconds_sample;        /* wall time of each ECM step */
+    double seconds_tally;
+    double seconds_commute;
+    double seconds_prune_tree;
+} tusq_plan_stats_t;
+
+/* Run the Error Characterization Module on the host (Sec. III-A) and build
+ * the DFS-ordered instance tree (Sec. III-B):
+ *   1. for shot s and channel c draw r = word (c mod 4) of Philox4x64-10 at
+ *      counter (s, c/4, 0, 0), key (seed, 0); the outcome is the first k with
+ *      r < T_k, T_k = floor(cdf_k * 2^64) over the cumulative probabilities
+ *      (identity first, cdf_0 = 1 - sum p), the last threshold being 2^64-1;
+ *   2. tally identical ERs; 3. commute each distinct ER and re-tally;
+ *   4. prune (significant iff c >= alpha * c_max; min(beta, |C_I|) picks by a
+ *      partial Fisher-Yates over C_I in key order with draws from key
+ *      (seed, 2), j = i + r mod (|C_I| - i); weights c/S and
+ *      (c/S)(C_insig / sum picked c)); 5. sort instances by their event
+ *      lists, ended lists last, and record the branch slot between
+ *      neighbours.
+ * The result is independent of n_threads.  *out is released with
+ * tusq_plan_free. */
+int tusq_plan(const tusq_circuit *c, const tusq_plan_opts *opts, uint64_t shots,
+              uint64_t seed, tusq_plan_t **out);
+
+int tusq_plan_stats(const tusq_plan_t *p, tusq_plan_stats_t *out);
+
+/* Build a plan from a caller-supplied instance list instead of running the
+ * ECM: n_inst instances, instance i's events are [ev_off[i], ev_off[i+1])
+ * of ev_slot / ev_qubit / ev_pauli (slot in [0, G], qubit in [0, n), Pauli
+ * 1..3; at most one event per (slot, qubit)), with weights[i].  The
+ * instances are sorted into DFS order and the branch slots computed as in
+ * tusq_plan; counts are reported as 0.  Returns TUSQ_EINVAL on a malformed
+ * list (bad slot/qubit/Pauli, unsorted or duplicate (slot, qubit), two
+ * identical instances). */
+int tusq_plan_from_instances(const tusq_circuit *c, uint64_t n_inst, const uint64_t *ev_off,
+                             const int32_t *ev_slot, const int32_t *ev_qubit,
+                             const int32_t *ev_pauli, const double *weights, tusq_plan_t **out);
+
+/* Borrowed views of the kept instances, valid until tusq_plan_free:
+ * instance i's events are [ev_off[i], ev_off[i+1]) of ev_slot / ev_qubit /
+ * ev_pauli (slot j = before gate j, slot G = after the last gate), sorted by
+ * (slot, qubit); lcp[i] (i < n_inst - 1) is the branch slot between
+ * instances i and i+1. */
+int tusq_plan_export(const tusq_plan_t *p, uint64_t *n_inst, const uint64_t **ev_off,
+                     const int32_t **ev_slot, const int32_t **ev_qubit,
+                     const int32_t **ev_pauli, const uint64_t **counts,
+                     const double **weights, const int32_t **lcp);
+
+/* Borrowed views of an intermediate tally: stage 0 = raw ERs after
+ * tallying (a = channel index, b = outcome code, c unused), stage 1 =
+ * commuted event lists before pruning (a = slot, b = qubit, c = Pauli).
+ * Both are sorted (ended lists last). */
+int tusq_plan_export_tally(const tusq_plan_t *p, int stage, uint64_t *n, const uint64_t **off,
+                           const int32_t **a, const int32_t **b, const int32_t **c,
+                           const uint64_t **counts);
+
+int tusq_plan_n_qubits(const tusq_plan_t *p);
+void tusq_plan_free(tusq_plan_t *p);
+
+/* ------------------------------------------------------------ execution */
+
+typedef struct {
+    int precision;            /* enum tusq_precision (default C64) */
+    int max_window;           /* qubits per fused pass tile, 0 = default */
+    int traversal;            /* enum tusq_traversal */
+    int leaf_peek;            /* 1: last forward pass accumulates and skips its write */
+    int root_reset;           /* 1: a branch at slot 0 resets to |0..0> instead of uncomputing */
+    double drift_tol;         /* drift check threshold (1e-6); < 0 disables checks */
+    uint64_t snapshot_bytes;  /* device budget for LIFO branch snapshots */
+    int check_every;          /* reserved, 0 */
+} tusq_run_opts;
+
+/* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
+ * snapshot_bytes = 8 states. */
+void tusq_run_opts_default(tusq_run_opts *o);
+
+typedef struct {
+    uint64_t passes;              /* fused full-state passes launched */
+    uint64_t gate_apps;           /* gate applications executed (fwd + uncompute) */
+    uint64_t pauli_apps;          /* Pauli applications executed */
+    uint64_t leaf_passes;
+    uint64_t checks;              /* drift checks evaluated */
+    uint64_t restores;            /* snapshot restores taken (device-decided) */
+    uint64_t unrecovered;         /* drift above tolerance with no snapshot */
+    uint64_t resets;              /* root resets */
+    uint64_t kernel_launches;
+    double max_drift;             /* largest drift measure seen */
+    double state_bytes;           /* bytes of one state */
+    double algorithmic_bytes;     /* HBM bytes the passes must move (reads + writes) */
+    double program_bytes;         /* device program copied host->device at create */
+} tusq_run_info_t;
+
+/* Compile a plan into a device program for the current device and allocate
+ * the state, the snapshot pool and the check records on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Host-side work is the
+ * schedule compilation (fused passes split at branch slots); the program
+ * is copied to the device once. */
+int tusq_exec_create(const tusq_plan_t *p, const tusq_run_opts *opts, void *cuda_stream,
+                     tusq_exec **out);
+
+/* Enqueue one DFTT traversal on `cuda_stream`: probs_dev (caller-owned
+ * device buffer of 2^n doubles) is zeroed and receives
+ * sum_i w_i |psi_i(x)|^2.  Stream-ordered; returns after enqueueing.  Drift
+ * checks and restores are decided on the device. */
+int tusq_exec_launch(tusq_exec *e, double *probs_dev, void *cuda_stream);
+
+/* Synchronise the stream of the last launch and fill *info; returns
+ * TUSQ_EDRIFT if a check failed where no snapshot was available, or
+ * TUSQ_ETIMEOUT if a device wait expired. */
+int tusq_exec_finish(tusq_exec *e, tusq_run_info_t *info);
+
+/* Host only (no GPU needed): compile the plan's device program with `opts`
+ * and report what a launch would execute -- passes, gate and Pauli
+ * applications, leaf passes, checks, resets, kernel launches and the
+ * algorithmic HBM bytes (state reads/writes of every pass, accumulator
+ * traffic of leaf passes).  Counters that only the device knows
+ * (restores, drift) are zero. */
+int tusq_compile_stats(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run_info_t *out);
+
+/* Profiling: when on, the next launches record a CUDA event pair around
+ * every fused pass on the launch stream.  After tusq_exec_finish,
+ * tusq_exec_pass_profile returns borrowed arrays (valid until the next
+ * launch or tusq_exec_free) of the last launch: per pass, its device time
+ * in ms and its algorithmic HBM bytes (state read + writes, accumulator
+ * traffic of leaf passes). */
+int tusq_exec_set_profiling(tusq_exec *e, int on);
+int tusq_exec_pass_profile(tusq_exec *e, uint64_t *n_passes, const float **ms,
+                           const double **bytes);
+
+/* Host hook for tests: add `delta` to the recorded norm of every record
+ * taken from now on (0 = off).  Forces the drift path without touching the
+ * device state. */
+int tusq_exec_set_record_bias(tusq_exec *e, double delta);
+
+void tusq_exec_free(tusq_exec *e);
+
+/* tusq_exec_create + launch + finish + free. */
+int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
+             void *cuda_stream);
+
+/* -------------------------------------------------------------- serving */
+
+/* A serving loop that admits jobs while their device footprint
+ * (state + accumulator + snapshots) fits hbm_budget_bytes, runs admitted
+ * jobs concurrently on `n_streams` CUDA streams of the current device and
+ * records each job's latency (submit to completion). */
+int tusq_server_create(size_t hbm_budget_bytes, int n_streams, tusq_server **out);
+
+/* Queue a job; the plan must stay alive until the job completes.  probs_dev
+ * is a caller-owned device buffer of 2^n doubles.  Returns TUSQ_ENOMEM_ADMIT
+ * if the job alone can never fit the budget. */
+int tusq_submit(tusq_server *s, const tusq_plan_t *p, const tusq_run_opts *opts,
+                double *probs_dev, uint64_t *job_id);
+
+/* Non-blocking: *done = 1 once finished (latency_s then set). */
+int tusq_poll(tusq_server *s, uint64_t job_id, int *done, double *latency_s);
+
+/* Block until every submitted job is done. */
+int tusq_server_drain(tusq_server *s);
+
+void tusq_server_free(tusq_server *s);
+
+/* Thread-local message for the last non-OK status on this thread. */
+const char *tusq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,607 @@
+// Schedule compiler: turns a plan (DFS-ordered instances and branch slots)
+// into the device program of one DFTT traversal (Sec. III-B): forward
+// segments split at the branch slots that will be revisited, uncompute
+// segments back to each branch slot, fused passes over qubit windows, and
+// register stages inside each pass.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <stdexcept>
+
+#include "internal.h"
+#include "program.h"
+
+namespace tusq {
+
+using cd = std::complex<double>;
+
+namespace {
+
+// ----------------------------------------------------------------- host ops
+
+enum HType { H_MAT1 = 0, H_MAT2 = 1, H_DIAG = 2 };
+
+struct HOp {
+    int type = H_MAT1;
+    int q0 = 0, q1 = -1;          // MAT2: basis index 2*bit(q0) + bit(q1)
+    bool pauli = false;
+    int key = 0;                  // canonical position: 2*slot for events, 2*slot+1 for gates
+    int uid = 0;                  // identity within the instance (for set differences)
+    cd m[16];
+    double phi0 = 0;              // DIAG, in turns
+    std::vector<std::pair<uint64_t, double>> terms;   // (global mask, turns)
+    uint64_t qmask() const {
+        if (type == H_DIAG) {
+            uint64_t m = 0;
+            for (auto &t : terms) m |= t.first;
+            return m;
+        }
+        return (1ULL << q0) | (q1 >= 0 ? (1ULL << q1) : 0);
+    }
+};
+
+const double kPi = 3.14159265358979323846;
+
+void gate_matrix(const Gate &g, cd *m) {
+    const cd I(0, 1);
+    double r = 1.0 / std::sqrt(2.0);
+    for (int k = 0; k < 16; ++k) m[k] = 0;
+    switch (g.kind) {
+    case TUSQ_H: m[0] = r; m[1] = r; m[2] = r; m[3] = -r; break;
+    case TUSQ_X: m[1] = 1; m[2] = 1; break;
+    case TUSQ_Y: m[1] = -I; m[2] = I; break;
+    case TUSQ_RX: {
+        double c = std::cos(g.p[0] / 2), s = std::sin(g.p[0] / 2);
+        m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
+    }
+    case TUSQ_RY: {
+        double c = std::cos(g.p[0] / 2), s = std::sin(g.p[0] / 2);
+        m[0] = c; m[1] = -s; m[2] = s; m[3] = c; break;
+    }
+    case TUSQ_U1Q: for (int k = 0; k < 4; ++k) m[k] = cd(g.p[2 * k], g.p[2 * k + 1]); break;
+    case TUSQ_CX: m[0] = 1; m[5] = 1; m[11] = 1; m[14] = 1; break;
+    case TUSQ_U2Q: for (int k = 0; k < 16; ++k) m[k] = cd(g.p[2 * k], g.p[2 * k + 1]); break;
+    default: throw std::logic_error("gate_matrix: not a dense kind");
+    }
+}
+
+// Diagonal gates as exp(2 pi i (phi0 + sum_k phi_k parity(x & mask_k))).
+void gate_diag(const Gate &g, HOp &op) {
+    uint64_t a = 1ULL << g.q0, b = g.q1 >= 0 ? 1ULL << g.q1 : 0;
+    switch (g.kind) {
+    case TUSQ_Z: op.terms = {{a, 0.5}}; break;
+    case TUSQ_S: op.terms = {{a, 0.25}}; break;
+    case TUSQ_SDG: op.terms = {{a, -0.25}}; break;
+    case TUSQ_T: op.terms = {{a, 0.125}}; break;
+    case TUSQ_TDG: op.terms = {{a, -0.125}}; break;
+    case TUSQ_RZ:      // diag(e^{-it/2}, e^{it/2})
+        op.phi0 = -g.p[0] / (4 * kPi); op.terms = {{a, g.p[0] / (2 * kPi)}}; break;
+    case TUSQ_CZ:      // pi * x_a x_b = (pi/2)(x_a + x_b - (x_a xor x_b))
+        op.terms = {{a, 0.25}, {b, 0.25}, {a | b, -0.25}}; break;
+    case TUSQ_RZZ:     // exp(-i t/2 (-1)^(x_a xor x_b))
+        op.phi0 = -g.p[0] / (4 * kPi); op.terms = {{a | b, g.p[0] / (2 * kPi)}}; break;
+    default: throw std::logic_error("gate_diag: not a diagonal kind");
+    }
+}
+
+HOp gate_op(const Gate &g, int j) {
+    HOp op;
+    op.key = 2 * j + 1;
+    op.q0 = g.q0;
+    op.q1 = g.q1;
+    if (is_diagonal(g.kind)) {
+        op.type = H_DIAG;
+        gate_diag(g, op);
+    } else {
+        op.type = is_two_qubit(g.kind) ? H_MAT2 : H_MAT1;
+        gate_matrix(g, op.m);
+    }
+    return op;
+}
+
+HOp pauli_op(int slot, int q, int p) {
+    HOp op;
+    op.key = 2 * slot;
+    op.q0 = q;
+    op.pauli = true;
+    const cd I(0, 1);
+    if (p == 3) {
+        op.type = H_DIAG;
+        op.terms = {{1ULL << q, 0.5}};
+    } else {
+        op.type = H_MAT1;
+        for (auto &z : op.m) z = 0;
+        if (p == 1) { op.m[1] = 1; op.m[2] = 1; }
+        else { op.m[1] = -I; op.m[2] = I; }
+    }
+    return op;
+}
+
+HOp inverse(const HOp &o) {
+    HOp r = o;
+    if (o.type == H_DIAG) {
+        r.phi0 = -o.phi0;
+        for (auto &t : r.terms) t.second = -t.second;
+    } else {
+        int d = o.type == H_MAT1 ? 2 : 4;
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) r.m[d * i + k] = std::conj(o.m[d * k + i]);
+    }
+    return r;
+}
+
+// --------------------------------------------------------- pass scheduling
+
+struct Pass {
+    std::vector<int> win;          // global qubits, ascending
+    std::vector<HOp> ops;          // in application order
+};
+
+// Greedy list scheduling over the dependence DAG of `ops` (two ops depend
+// on each other if they share a qubit, unless both are diagonal): a group
+// takes every ready op whose bits (qubits_of, for non-diagonal ops) fit its
+// window of `cap` bits, growing the window while there is room, in list
+// order; diagonal ops fit any window.
+template <class QubitsOf>
+std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uint64_t forced,
+                                       QubitsOf qubits_of, std::vector<uint64_t> *wins) {
+    const int m = (int)ops.size();
+    std::vector<std::vector<int>> preds(m);
+    std::vector<uint64_t> qm(m);
+    for (int b = 0; b < m; ++b) qm[b] = ops[b].qmask();
+    for (int b = 0; b < m; ++b) {
+        for (int a = 0; a < b; ++a) {
+            if (ops[a].type == H_DIAG && ops[b].type == H_DIAG) continue;
+            if (qm[a] & qm[b]) preds[b].push_back(a);
+        }
+    }
+    std::vector<char> done(m, 0);
+    int left = m;
+    std::vector<std::vector<int>> groups;
+    while (left > 0) {
+        uint64_t W = forced;
+        std::vector<int> g;
+        bool progress = true;
+        while (progress) {
+            progress = false;
+            for (int b = 0; b < m; ++b) {
+                if (done[b]) continue;
+                bool ready = true;
+                for (int a : preds[b]) if (!done[a]) { ready = false; break; }
+                if (!ready) continue;
+                if (ops[b].type != H_DIAG) {
+                    uint64_t q = qubits_of(ops[b]);
+                    if ((q & ~W) != 0) {
+                        if (__builtin_popcountll(W | q) > cap) continue;
+                        W |= q;
+                    }
+                }
+                done[b] = 1;
+                --left;
+                g.push_back(b);
+                progress = true;
+            }
+        }
+        if (g.empty()) throw std::logic_error("schedule: no progress (gate wider than window?)");
+        groups.push_back(g);
+        if (wins) wins->push_back(W);
+    }
+    return groups;
+}
+
+// Merge neighbouring diagonal ops and neighbouring 1q matrices on the same
+// qubit inside one op list (application order).
+std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
+    std::vector<HOp> out;
+    for (const HOp &o : in) {
+        if (!out.empty()) {
+            HOp &p = out.back();
+            if (o.type == H_DIAG && p.type == H_DIAG) {
+                p.phi0 += o.phi0;
+                for (auto &t : o.terms) {
+                    bool hit = false;
+                    for (auto &u : p.terms)
+                        if (u.first == t.first) { u.second += t.second; hit = true; break; }
+                    if (!hit) p.terms.push_back(t);
+                }
+                p.pauli = false;
+                continue;
+            }
+            if (o.type == H_MAT1 && p.type == H_MAT1 && o.q0 == p.q0) {
+                cd r[4];
+                for (int i = 0; i < 2; ++i)
+                    for (int k = 0; k < 2; ++k)
+                        r[2 * i + k] = o.m[2 * i] * p.m[k] + o.m[2 * i + 1] * p.m[2 + k];
+                for (int k = 0; k < 4; ++k) p.m[k] = r[k];
+                p.pauli = false;
+                continue;
+            }
+        }
+        out.push_back(o);
+    }
+    return out;
+}
+
+// ------------------------------------------------------------- encoding
+
+inline uint32_t swz(uint32_t e, bool c128) {
+    if (c128) return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
+    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
+}
+
+uint64_t to_fixed(double turns, bool c128) {
+    double f = turns - std::floor(turns);
+    if (c128) {
+        long double v = (long double)f * 9223372036854775808.0L;   // 2^63
+        return (uint64_t)llroundl(v) & 0x7FFFFFFFFFFFFFFFULL;
+    }
+    return (uint64_t)llround(f * 2147483648.0) & 0x7FFFFFFFULL;     // 2^31
+}
+
+struct Encoder {
+    Program &prog;
+    int n;
+    bool c128;
+    int V;
+    int Lmax;
+
+    // Encode one pass (window + ops already in application order) into
+    // PassDescs (several if the register stages exceed kMaxStages).
+    void emit(const std::vector<int> &win, const std::vector<HOp> &ops_in, uint32_t flags,
+              double leaf_w, int snap, std::vector<int> &pass_ids) {
+        const int L = (int)win.size();
+        int local[64];
+        for (int i = 0; i < 64; ++i) local[i] = -1;
+        for (int i = 0; i < L; ++i) local[win[i]] = i;
+        std::vector<HOp> ops = merge_ops(ops_in);
+        // stage scheduling over local bits
+        auto lq = [&](const HOp &o) -> uint64_t {
+            if (o.type == H_DIAG) return 0;
+            uint64_t m = 1ULL << local[o.q0];
+            if (o.type == H_MAT2) m |= 1ULL << local[o.q1];
+            return m;
+        };
+        const int v = std::min(V, L);
+        std::vector<uint64_t> swin;
+        std::vector<std::vector<int>> stages;
+        if (!ops.empty()) stages = schedule(ops, v, 0, lq, &swin);
+        size_t s0 = 0;
+        do {
+            size_t s1 = std::min(stages.size(), s0 + kMaxStages);
+            PassDesc pd;
+            std::memset(&pd, 0, sizeof pd);
+            pd.L = L;
+            pd.n_stages = (int)(s1 - s0);
+            bool last = (s1 >= stages.size());
+            pd.flags = last ? flags : PF_WRITE;
+            pd.leaf_w = leaf_w;
+            pd.snap = snap;
+            for (int i = 0; i < L; ++i) pd.win[i] = (uint8_t)win[i];
+            int ncw = 0;
+            for (int q = 0; q < n; ++q)
+                if (local[q] < 0) pd.cw[ncw++] = (uint8_t)q;
+            pd.n_cw = ncw;
+            pd.ntiles = 1ULL << ncw;
+            const int T = 1 << (L - v);
+            for (int i = 0; i < (1 << v); ++i) {
+                uint32_t e = (uint32_t)i * T;
+                uint64_t g = 0;
+                for (int b = 0; b < L; ++b)
+                    if (e >> b & 1) g |= 1ULL << win[b];
+                pd.grow[i] = g;
+                pd.srow[i] = (uint16_t)swz(e, c128);
+            }
+            for (size_t s = s0; s < s1; ++s) {
+                StageDesc &sd = pd.st[s - s0];
+                uint64_t R = swin[s];
+                // fill up to v register bits with the highest unused local bits
+                for (int b = L - 1; b >= 0 && __builtin_popcountll(R) < v; --b) R |= 1ULL << b;
+                int nr = 0, nc = 0;
+                for (int b = 0; b < L; ++b) {
+                    if (R >> b & 1) sd.rbits[nr++] = (uint8_t)b;
+                    else sd.cpos[nc++] = (uint8_t)b;
+                }
+                for (int i = 0; i < v; ++i) sd.greg[i] = 1ULL << win[sd.rbits[i]];
+                for (int r = 0; r < (1 << v); ++r) {
+                    uint32_t e = 0;
+                    for (int i = 0; i < v; ++i)
+                        if (r >> i & 1) e |= 1u << sd.rbits[i];
+                    sd.sr[r] = (uint16_t)swz(e, c128);
+                }
+                int regidx[64];
+                for (int i = 0; i < 64; ++i) regidx[i] = -1;
+                for (int i = 0; i < v; ++i) regidx[sd.rbits[i]] = i;
+                sd.op_begin = (uint32_t)prog.ops.size();
+                for (int oi : stages[s]) {
+                    const HOp &o = ops[oi];
+                    DevOp d;
+                    std::memset(&d, 0, sizeof d);
+                    if (o.type == H_MAT1) {
+                        d.type = OP_MAT1;
+                        d.a = regidx[local[o.q0]];
+                        d.mat = (uint32_t)(prog.mats.size() / 32);
+                        for (int k = 0; k < 4; ++k) { prog.mats.push_back(o.m[k].real()); prog.mats.push_back(o.m[k].imag()); }
+                        for (int k = 4; k < 16; ++k) { prog.mats.push_back(0); prog.mats.push_back(0); }
+                    } else if (o.type == H_MAT2) {
+                        int ra = regidx[local[o.q0]], rb = regidx[local[o.q1]];
+                        // device basis: k = bit_lo + 2 bit_hi over register bits lo < hi;
+                        // gate basis: l = 2 bit(q0) + bit(q1)
+                        int lo = std::min(ra, rb), hi = std::max(ra, rb);
+                        d.type = OP_MAT2;
+                        d.a = lo;
+                        d.b = hi;
+                        d.mat = (uint32_t)(prog.mats.size() / 32);
+                        auto l_of = [&](int k) {
+                            int blo = k & 1, bhi = k >> 1;
+                            int b0 = (ra == lo) ? blo : bhi, b1 = (rb == lo) ? blo : bhi;
+                            return 2 * b0 + b1;
+                        };
+                        for (int r = 0; r < 4; ++r)
+                            for (int c = 0; c < 4; ++c) {
+                                cd z = o.m[4 * l_of(r) + l_of(c)];
+                                prog.mats.push_back(z.real());
+                                prog.mats.push_back(z.imag());
+                            }
+                    } else {
+                        d.type = OP_DIAG;
+                        d.phi0 = to_fixed(o.phi0, c128);
+                        // register mask of each term, sort by it
+                        std::vector<std::pair<int, std::pair<uint64_t, double>>> t;
+                        for (auto &term : o.terms) {
+                            int mu = 0;
+                            for (int i = 0; i < v; ++i)
+                                if (term.first & sd.greg[i]) mu |= 1 << i;
+                            t.push_back({mu, term});
+                        }
+                        std::stable_sort(t.begin(), t.end(), [](auto &x, auto &y) { return x.first < y.first; });
+                        d.term_begin = (uint32_t)prog.term_mask.size();
+                        int k = 0;
+                        for (int mu = 0; mu <= 32; ++mu) {
+                            while (k < (int)t.size() && t[k].first < mu) ++k;
+                            d.csr[mu] = (uint16_t)k;
+                        }
+                        d.csr[33] = (uint16_t)t.size();
+                        for (auto &x : t) {
+                            prog.term_mask.push_back(x.second.first);
+                            prog.term_phi.push_back(to_fixed(x.second.second, c128));
+                        }
+                    }
+                    prog.ops.push_back(d);
+                }
+                sd.op_count = (uint32_t)(prog.ops.size() - sd.op_begin);
+            }
+            pass_ids.push_back((int)prog.passes.size());
+            prog.passes.push_back(pd);
+            s0 = s1;
+        } while (s0 < stages.size());
+    }
+};
+
+// ---------------------------------------------------------------- traversal
+
+struct Compiler {
+    const tusq_plan_t &P;
+    const CompileOpts &co;
+    Program &prog;
+    Encoder enc;
+    int G, n, L;
+    uint64_t forced;
+    std::vector<HOp> gate_ops;
+
+    Compiler(const tusq_plan_t &p, const CompileOpts &c, Program &pr)
+        : P(p), co(c), prog(pr), enc{pr, p.n, c.precision == TUSQ_C128,
+                                     c.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, 0} {
+        G = P.G;
+        n = P.n;
+        // at most 256 threads x 2^V registers per CTA: 2^13 (c64), 2^12 (c128)
+        int lmax = co.precision == TUSQ_C128 ? 12 : 13;
+        if (co.max_window > 0) lmax = std::min(co.max_window, lmax);
+        L = std::min(lmax, n);
+        enc.Lmax = L;
+        // the lowest qubits stay in every window (contiguous 128-byte runs),
+        // leaving room for any two-qubit gate
+        int nf = std::min(co.precision == TUSQ_C128 ? 3 : 4, std::max(L - 2, 0));
+        forced = (nf >= 64) ? ~0ULL : ((1ULL << nf) - 1);
+        for (int j = 0; j < G; ++j) gate_ops.push_back(gate_op(P.gates[j], j));
+    }
+
+    // Instance i's ops with canonical position in [2*a, 2*b) i.e. events at
+    // slots a..b-1 and gates a..b-1, in canonical order.
+    std::vector<HOp> segment(uint64_t i, int a, int b) {
+        std::vector<HOp> out;
+        uint64_t e = P.ev_off[i], e1 = P.ev_off[i + 1];
+        while (e < e1 && P.ev_slot[e] < a) ++e;
+        for (int j = a; j < b; ++j) {
+            for (; e < e1 && P.ev_slot[e] == j; ++e) {
+                HOp o = pauli_op(j, P.ev_qubit[e], P.ev_pauli[e]);
+                o.uid = -(int)(e - P.ev_off[i]) - 1;
+                out.push_back(o);
+            }
+            if (j < G) {
+                HOp o = gate_ops[j];
+                o.uid = j;
+                out.push_back(o);
+            }
+        }
+        return out;
+    }
+
+    void count(const std::vector<HOp> &ops) {
+        for (auto &o : ops) {
+            if (o.pauli) prog.pauli_apps++;
+            else prog.gate_apps++;
+        }
+    }
+
+    void push_passes(const std::vector<int> &ids) {
+        prog.passes_count += ids.size();
+        for (int id : ids) prog.steps.push_back(Step{ST_PASS, id, 0, -1, 0});
+    }
+
+    // Schedule a list of ops into passes; the last pass gets `last_flags`.
+    // Returns the ops of the last pass (application order) through last_ops.
+    void emit_ops(const std::vector<HOp> &ops, uint32_t last_flags, double w, int snap,
+                  std::vector<HOp> *last_ops) {
+        count(ops);
+        std::vector<uint64_t> wins;
+        auto gq = [](const HOp &o) { return o.type == H_DIAG ? 0ULL : o.qmask(); };
+        std::vector<std::vector<int>> groups;
+        if (!ops.empty()) groups = schedule(ops, L, forced, gq, &wins);
+        if (groups.empty()) {
+            // nothing to apply: an empty pass carries the flags
+            std::vector<int> win;
+            for (int b = 0; b < L; ++b) win.push_back(b);
+            std::vector<int> ids;
+            enc.emit(win, {}, last_flags, w, snap, ids);
+            push_passes(ids);
+            if (last_ops) last_ops->clear();
+            return;
+        }
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            uint64_t W = wins[gi];
+            for (int b = 0; __builtin_popcountll(W) < L && b < n; ++b) W |= 1ULL << b;
+            std::vector<int> win;
+            for (int b = 0; b < n; ++b)
+                if (W >> b & 1) win.push_back(b);
+            std::vector<HOp> pops;
+            for (int oi : groups[gi]) pops.push_back(ops[oi]);
+            bool last = (gi + 1 == groups.size());
+            std::vector<int> ids;
+            enc.emit(win, pops, last ? last_flags : PF_WRITE, w, snap, ids);
+            push_passes(ids);
+            if (last && last_ops) *last_ops = pops;
+        }
+    }
+
+    void run() {
+        const uint64_t N = P.n_inst();
+        prog.steps.push_back(Step{ST_INIT, 0, 0, -1, 0});
+        if (N == 0) return;
+        // LIFO of the branch nodes on the current root-to-leaf path that will
+        // be returned to: their slot, stack depth, snapshot slot (-1: none)
+        // and whether their norm/checksum was recorded.
+        struct Rec { int slot, depth, snap; bool recorded; };
+        std::vector<Rec> stack;
+        const bool scratch = co.traversal == TUSQ_FROM_SCRATCH;
+        const bool snap_policy = co.traversal == TUSQ_DFTT_SNAPSHOT;
+        const bool track = !scratch && (co.checks || snap_policy);
+        // reused[i]: the branch node of pair (i, i+1) is returned to again,
+        // i.e. the next branch slot that is not larger is equal to it
+        // (next smaller-or-equal element, by a monotonic stack).
+        std::vector<char> reused(N > 1 ? N - 1 : 0, 0);
+        {
+            std::vector<uint64_t> mono;
+            for (uint64_t i = N > 1 ? N - 1 : 0; i-- > 0;) {
+                while (!mono.empty() && P.lcp[mono.back()] > P.lcp[i]) mono.pop_back();
+                reused[i] = !mono.empty() && P.lcp[mono.back()] == P.lcp[i];
+                mono.push_back(i);
+            }
+        }
+        for (uint64_t i = 0; i < N; ++i) {
+            int t_in = (i == 0 || scratch) ? 0 : P.lcp[i - 1];
+            // future branch slots on this path: running minima of the next
+            // branch slots, above t_in
+            std::vector<int> chain;
+            if (track) {
+                int m = G + 2;
+                for (uint64_t k = i; k + 1 < N; ++k) {
+                    int t = P.lcp[k];
+                    if (t <= t_in) break;
+                    if (t < m) { chain.push_back(t); m = t; }
+                }
+                std::reverse(chain.begin(), chain.end());
+            }
+            std::vector<int> bounds;
+            bounds.push_back(t_in);
+            for (int s : chain) if (s > bounds.back()) bounds.push_back(s);
+            bounds.push_back(G + 1);
+            std::vector<HOp> leaf_ops;
+            bool last_inst = (i + 1 == N);
+            for (size_t s = 0; s + 1 < bounds.size(); ++s) {
+                std::vector<HOp> ops = segment(i, bounds[s], bounds[s + 1]);
+                bool final_seg = (s + 2 == bounds.size());
+                if (!final_seg) {
+                    // the pass that ends at a future branch node records it
+                    int depth = (int)stack.size();
+                    int snap = depth < co.snapshots ? depth : -1;
+                    bool rec = co.checks && !(snap_policy && snap >= 0);
+                    uint32_t fl = PF_WRITE | (rec ? PF_REDUCE : 0u) | (snap >= 0 ? PF_SNAPSHOT : 0u);
+                    emit_ops(ops, fl, 0.0, snap, nullptr);
+                    if (rec) prog.steps.push_back(Step{ST_RECORD, 0, depth, snap, 0});
+                    stack.push_back(Rec{bounds[s + 1], depth, snap, rec});
+                    prog.max_depth = std::max(prog.max_depth, depth + 1);
+                } else {
+                    bool peek = co.leaf_peek && !scratch && !last_inst;
+                    uint32_t fl = PF_LEAF | (peek ? 0u : PF_WRITE);
+                    if (scratch || last_inst) fl &= ~PF_WRITE;   // nothing reads the state afterwards
+                    emit_ops(ops, fl, P.weights[i], -1, &leaf_ops);
+                    prog.leaf_passes++;
+                    if (!peek) leaf_ops.clear();
+                    if (scratch || last_inst) leaf_ops.clear();
+                }
+            }
+            if (last_inst) break;
+            int t = scratch ? 0 : P.lcp[i];
+            if (scratch || (co.root_reset && t == 0)) {
+                prog.steps.push_back(Step{ST_INIT, 0, 0, -1, 0});
+                prog.resets++;
+                stack.clear();
+                continue;
+            }
+            while (!stack.empty() && stack.back().slot > t) stack.pop_back();
+            if (track && (stack.empty() || stack.back().slot != t))
+                throw std::logic_error("compile: branch slot was not materialised");
+            return_to(i, t, leaf_ops, stack, snap_policy);
+            // a node that no later pair branches at is done with
+            if (track && !reused[i]) stack.pop_back();
+        }
+    }
+
+    template <class Stack>
+    void return_to(uint64_t i, int t, const std::vector<HOp> &leaf_ops, Stack &stack, bool snap_policy) {
+            const int G = this->G;
+            if (snap_policy && !stack.empty() && stack.back().snap >= 0) {
+                // the branch node's own snapshot: one copy pass back to it
+                prog.steps.push_back(Step{ST_RESTORE, 0, stack.back().depth, stack.back().snap, -1});
+                prog.restores++;
+                return;
+            }
+            // uncompute instance i back to slot t (ops at slots >= t not
+            // already undone by the leaf pass that skipped its write)
+            std::vector<HOp> all = segment(i, t, G + 1);
+            std::vector<HOp> undo;
+            for (auto it = all.rbegin(); it != all.rend(); ++it) {
+                bool skipped = false;
+                for (auto &lo : leaf_ops)
+                    if (lo.uid == it->uid) { skipped = true; break; }
+                if (!skipped) undo.push_back(inverse(*it));
+            }
+            if (undo.empty()) return;     // the state never left the branch node
+            if (!co.checks || stack.empty() || !stack.back().recorded) {
+                emit_ops(undo, PF_WRITE, 0.0, -1, nullptr);
+                return;
+            }
+            int depth = stack.back().depth;
+            int snap = stack.back().snap;
+            emit_ops(undo, PF_WRITE | PF_REDUCE, 0.0, -1, nullptr);
+            int chk = prog.n_checks++;
+            prog.steps.push_back(Step{ST_CHECK, 0, depth, snap, chk});
+            if (snap >= 0) prog.steps.push_back(Step{ST_RESTORE, 0, depth, snap, chk});
+    }
+
+};
+
+}  // namespace
+
+void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog) {
+    prog = Program{};
+    prog.n = P.n;
+    prog.precision = co.precision;
+    prog.reg_bits = co.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64;
+    prog.n_snapshots = co.snapshots;
+    Compiler c(P, co, prog);
+    c.run();
+}
+
+}  // namespace tusq

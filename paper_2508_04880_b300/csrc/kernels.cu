@@ -1,0 +1,457 @@
+// CUDA kernels of the DFTT engine (sm_103a).
+//
+// pass_kernel: one full-state pass.  The state is cut into tiles of 2^L
+// amplitudes that share every index bit outside a window of L qubits
+// (the window always contains the lowest qubits, so each tile is a set of
+// contiguous 128-byte runs).  A CTA loads a tile into shared memory with
+// coalesced loads, runs its register stages -- each thread gathers 2^V
+// amplitudes that differ in the stage's V register bits, applies the
+// stage's gates in registers (2x2, 4x4, diagonal phase runs), scatters
+// them back -- and writes the tile back, optionally also to a snapshot,
+// adding w|psi|^2 into the FP64 output (leaf) and producing partial sums
+// of the norm and a checksum (drift check).  Shared-memory addresses are
+// XOR-swizzled so that the gathers of every stage layout spread over banks.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "program.h"
+
+namespace tusq {
+
+template <typename R> struct C2T;
+template <> struct C2T<float> { using type = float2; };
+template <> struct C2T<double> { using type = double2; };
+
+template <typename C2> __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+    C2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C2> __device__ __forceinline__ C2 cmad(C2 a, C2 b, C2 c) {
+    // a * b + c
+    C2 r;
+    r.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+    r.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+    return r;
+}
+
+template <typename R> __device__ __forceinline__ typename C2T<R>::type load_mat(const double *m, int k);
+template <> __device__ __forceinline__ float2 load_mat<float>(const double *m, int k) {
+    return make_float2((float)__ldg(m + 2 * k), (float)__ldg(m + 2 * k + 1));
+}
+template <> __device__ __forceinline__ double2 load_mat<double>(const double *m, int k) {
+    return make_double2(__ldg(m + 2 * k), __ldg(m + 2 * k + 1));
+}
+
+// 2x2 on register bit B.
+template <int V, int B, typename C2>
+__device__ __forceinline__ void apply1(C2 (&a)[1 << V], C2 m0, C2 m1, C2 m2, C2 m3) {
+#pragma unroll
+    for (int r = 0; r < (1 << V); ++r) {
+        if (r & (1 << B)) continue;
+        C2 x = a[r], y = a[r | (1 << B)];
+        C2 zero;
+        zero.x = 0;
+        zero.y = 0;
+        a[r] = cmad(m0, x, cmul(m1, y));
+        a[r | (1 << B)] = cmad(m2, x, cmul(m3, y));
+        (void)zero;
+    }
+}
+
+// 4x4 on register bits A < B, basis k = bit_A + 2 bit_B.
+template <int V, int A, int B, typename C2>
+__device__ __forceinline__ void apply2(C2 (&a)[1 << V], const C2 (&m)[16]) {
+#pragma unroll
+    for (int r = 0; r < (1 << V); ++r) {
+        if (r & ((1 << A) | (1 << B))) continue;
+        const int i0 = r, i1 = r | (1 << A), i2 = r | (1 << B), i3 = r | (1 << A) | (1 << B);
+        C2 v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
+        a[i0] = cmad(m[0], v0, cmad(m[1], v1, cmad(m[2], v2, cmul(m[3], v3))));
+        a[i1] = cmad(m[4], v0, cmad(m[5], v1, cmad(m[6], v2, cmul(m[7], v3))));
+        a[i2] = cmad(m[8], v0, cmad(m[9], v1, cmad(m[10], v2, cmul(m[11], v3))));
+        a[i3] = cmad(m[12], v0, cmad(m[13], v1, cmad(m[14], v2, cmul(m[15], v3))));
+    }
+}
+
+template <int V, typename C2>
+__device__ __forceinline__ void dispatch1(C2 (&a)[1 << V], int b, C2 m0, C2 m1, C2 m2, C2 m3) {
+    switch (b) {
+    case 0: apply1<V, 0>(a, m0, m1, m2, m3); break;
+    case 1: if constexpr (V > 1) apply1<V, 1>(a, m0, m1, m2, m3); break;
+    case 2: if constexpr (V > 2) apply1<V, 2>(a, m0, m1, m2, m3); break;
+    case 3: if constexpr (V > 3) apply1<V, 3>(a, m0, m1, m2, m3); break;
+    case 4: if constexpr (V > 4) apply1<V, 4>(a, m0, m1, m2, m3); break;
+    default: break;
+    }
+}
+
+template <int V, typename C2>
+__device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], int lo, int hi, const C2 (&m)[16]) {
+#define TUSQ_CASE2(X, Y) \
+    case X * 8 + Y: if constexpr (V > Y) apply2<V, X, Y>(a, m); break;
+    switch (lo * 8 + hi) {
+        TUSQ_CASE2(0, 1) TUSQ_CASE2(0, 2) TUSQ_CASE2(0, 3) TUSQ_CASE2(0, 4)
+        TUSQ_CASE2(1, 2) TUSQ_CASE2(1, 3) TUSQ_CASE2(1, 4)
+        TUSQ_CASE2(2, 3) TUSQ_CASE2(2, 4)
+        TUSQ_CASE2(3, 4)
+    default: break;
+    }
+#undef TUSQ_CASE2
+}
+
+// Fixed-point phase -> (cos, sin) of 2 pi * phase.
+template <typename R> struct Phase;
+template <> struct Phase<float> {
+    using U = uint32_t;
+    static constexpr U kMask = 0x7FFFFFFFu;
+    __device__ static float2 unit(U p) {
+        float t = (float)(p & kMask) * 4.656612873077393e-10f;   // 2^-31 turns
+        float s, c;
+        sincospif(2.0f * t, &s, &c);
+        return make_float2(c, s);
+    }
+};
+template <> struct Phase<double> {
+    using U = uint64_t;
+    static constexpr U kMask = 0x7FFFFFFFFFFFFFFFull;
+    __device__ static double2 unit(U p) {
+        double t = (double)(p & kMask) * 1.0842021724855044e-19;  // 2^-63 turns
+        double s, c;
+        sincospi(2.0 * t, &s, &c);
+        return make_double2(c, s);
+    }
+};
+
+// Diagonal run on the 2^V registers of one thread.  gfix is the global
+// index of the thread's register 0 (register bits cleared).  The angle of
+// register r is A + sum_mu C[mu] parity(r & mu); the parity sums are
+// obtained from one Walsh-Hadamard transform of C (exact in fixed point:
+// sum_mu C[mu] parity(r & mu) = (sum C - WHT(C)[r]) / 2).
+template <typename R, int V>
+__device__ __forceinline__ void apply_diag(typename C2T<R>::type (&a)[1 << V], const DevOp &op,
+                                           const uint64_t *__restrict__ tmask,
+                                           const uint64_t *__restrict__ tphi, uint64_t gfix) {
+    using U = typename Phase<R>::U;
+    constexpr int NR = 1 << V;
+    U A = (U)op.phi0;
+    U C[NR];
+#pragma unroll
+    for (int mu = 0; mu < NR; ++mu) C[mu] = 0;
+    const uint32_t tb = op.term_begin;
+    for (int k = op.csr[0]; k < op.csr[1]; ++k) {
+        U ph = (U)__ldg(tphi + tb + k);
+        if (__popcll(gfix & __ldg(tmask + tb + k)) & 1) A += ph;
+    }
+#pragma unroll
+    for (int mu = 1; mu < NR; ++mu) {
+        for (int k = op.csr[mu]; k < op.csr[mu + 1]; ++k) {
+            U ph = (U)__ldg(tphi + tb + k);
+            bool c = __popcll(gfix & __ldg(tmask + tb + k)) & 1;
+            A += c ? ph : (U)0;
+            C[mu] += c ? (U)(0 - ph) : ph;
+        }
+    }
+    U sum = 0;
+#pragma unroll
+    for (int mu = 0; mu < NR; ++mu) sum += C[mu];
+#pragma unroll
+    for (int h = 1; h < NR; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            if (i & h) continue;
+            U x = C[i], y = C[i | h];
+            C[i] = x + y;
+            C[i | h] = x - y;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        U ang = A + ((U)(sum - C[r]) >> 1);
+        a[r] = cmul(a[r], Phase<R>::unit(ang));
+    }
+}
+
+__device__ __forceinline__ uint32_t swz(uint32_t e, bool c128) {
+    if (c128) return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
+    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
+}
+
+// Sign +-1 of the checksum weight of global index x (a 32-bit integer hash
+// of x folded to 32 bits; C. Wellons' "lowbias32" mixer).
+__device__ __forceinline__ float check_sign(uint64_t x) {
+    uint32_t h = (uint32_t)x ^ ((uint32_t)(x >> 32) * 0x9E3779B9u);
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return (h >> 31) ? -1.0f : 1.0f;
+}
+
+
+template <typename R, int V>
+__global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassArgs args) {
+    using C2 = typename C2T<R>::type;
+    constexpr int NR = 1 << V;
+    constexpr bool kC128 = sizeof(R) == 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
+    const PassDesc &d = args.d;
+    const int L = d.L;
+    const int tid = threadIdx.x;
+    C2 *state = reinterpret_cast<C2 *>(args.state);
+    C2 *snap = reinterpret_cast<C2 *>(args.snap);
+    const uint32_t flags = d.flags;
+
+    // this thread's part of a load row: local index tid -> global offset
+    uint64_t gthr = 0;
+    for (int b = 0; b < L - V; ++b)
+        if (tid >> b & 1) gthr |= 1ull << d.win[b];
+    const uint32_t sthr = swz((uint32_t)tid, kC128);
+
+    double red_n = 0.0, red_r = 0.0, red_i = 0.0;
+
+    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        uint64_t tb = 0;
+        for (int b = 0; b < d.n_cw; ++b)
+            if (t >> b & 1) tb |= 1ull << d.cw[b];
+        const uint64_t gbase = tb | gthr;
+        // load the tile
+#pragma unroll
+        for (int i = 0; i < NR; ++i) tile[sthr ^ d.srow[i]] = state[gbase | d.grow[i]];
+        __syncthreads();
+        for (int s = 0; s < d.n_stages; ++s) {
+            const StageDesc &sd = d.st[s];
+            if (sd.op_count == 0) continue;
+            // thread bits -> the stage's non-register local bits
+            uint32_t e = 0;
+            uint64_t gfix = tb;
+            for (int b = 0; b < L - V; ++b)
+                if (tid >> b & 1) {
+                    e |= 1u << sd.cpos[b];
+                    gfix |= 1ull << d.win[sd.cpos[b]];
+                }
+            const uint32_t sb = swz(e, kC128);
+            C2 a[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a[r] = tile[sb ^ sd.sr[r]];
+            for (uint32_t k = 0; k < sd.op_count; ++k) {
+                const DevOp &op = args.ops[sd.op_begin + k];
+                const int type = op.type;
+                if (type == OP_MAT1) {
+                    const double *m = args.mats + 32 * (size_t)op.mat;
+                    dispatch1<V>(a, op.a, load_mat<R>(m, 0), load_mat<R>(m, 1), load_mat<R>(m, 2),
+                                 load_mat<R>(m, 3));
+                } else if (type == OP_MAT2) {
+                    const double *m = args.mats + 32 * (size_t)op.mat;
+                    C2 mm[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) mm[q] = load_mat<R>(m, q);
+                    dispatch2<V>(a, op.a, op.b, mm);
+                } else {
+                    apply_diag<R, V>(a, op, args.tmask, args.tphi, gfix);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) tile[sb ^ sd.sr[r]] = a[r];
+            __syncthreads();
+        }
+        // store + epilogue
+        float pn = 0.f, pr = 0.f, pi = 0.f;
+        double dn = 0.0, dr = 0.0, di = 0.0;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const uint64_t g = gbase | d.grow[i];
+            C2 v = tile[sthr ^ d.srow[i]];
+            if (flags & PF_WRITE) state[g] = v;
+            if (flags & PF_SNAPSHOT) snap[g] = v;
+            if (flags & PF_LEAF) {
+                double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                args.acc[g] = fma(d.leaf_w, p, args.acc[g]);
+            }
+            if (flags & PF_REDUCE) {
+                float h = check_sign(g);
+                if constexpr (kC128) {
+                    dn += v.x * v.x + v.y * v.y;
+                    dr += h * v.x;
+                    di += h * v.y;
+                } else {
+                    pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
+                    pr = fmaf(h, v.x, pr);
+                    pi = fmaf(h, v.y, pi);
+                }
+            }
+        }
+        red_n += (double)pn + dn;
+        red_r += (double)pr + dr;
+        red_i += (double)pi + di;
+        __syncthreads();
+    }
+    if (flags & PF_REDUCE) {
+        // fixed-order block reduction: warp shuffles, then warp 0
+        __shared__ double wsum[3][32];
+        for (int off = 16; off > 0; off >>= 1) {
+            red_n += __shfl_down_sync(0xffffffffu, red_n, off);
+            red_r += __shfl_down_sync(0xffffffffu, red_r, off);
+            red_i += __shfl_down_sync(0xffffffffu, red_i, off);
+        }
+        const int warp = tid >> 5, lane = tid & 31, nw = (blockDim.x + 31) >> 5;
+        if (lane == 0) { wsum[0][warp] = red_n; wsum[1][warp] = red_r; wsum[2][warp] = red_i; }
+        __syncthreads();
+        if (tid == 0) {
+            double a0 = 0, a1 = 0, a2 = 0;
+            for (int w = 0; w < nw; ++w) { a0 += wsum[0][w]; a1 += wsum[1][w]; a2 += wsum[2][w]; }
+            args.partials[3 * blockIdx.x + 0] = a0;
+            args.partials[3 * blockIdx.x + 1] = a1;
+            args.partials[3 * blockIdx.x + 2] = a2;
+        }
+    }
+}
+
+// state <- |0..0>
+template <typename C2>
+__global__ void init_kernel(C2 *state, uint64_t dim) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        C2 z;
+        z.x = (i == 0) ? 1 : 0;
+        z.y = 0;
+        state[i] = z;
+    }
+}
+
+// Per-check record: norm2, cs_re, cs_im.  A record stores the sums at a
+// branch node on the way down; a check recomputes them after the
+// uncompute and stores max(|sqrt(n2) - sqrt(n2_ref)|, |cs - cs_ref|).
+__global__ void finalize_kernel(const double *partials, int nparts, double *records, int depth,
+                                int is_check, double *drift_log, int check, int *restore_flag,
+                                int has_snapshot, double tol, unsigned long long *counters,
+                                double record_bias) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double n2 = 0, cr = 0, ci = 0;
+    for (int b = 0; b < nparts; ++b) {
+        n2 += partials[3 * b];
+        cr += partials[3 * b + 1];
+        ci += partials[3 * b + 2];
+    }
+    double *rec = records + 4 * depth;
+    if (!is_check) {
+        rec[0] = n2 + record_bias;
+        rec[1] = cr;
+        rec[2] = ci;
+        return;
+    }
+    double dn = fabs(sqrt(n2) - sqrt(fmax(rec[0], 0.0)));
+    double dc = hypot(cr - rec[1], ci - rec[2]);
+    double drift = fmax(dn, dc);
+    drift_log[check] = drift;
+    int bad = drift > tol;
+    restore_flag[check] = bad && has_snapshot;
+    if (bad) {
+        if (has_snapshot) atomicAdd(counters + 0, 1ull);
+        else atomicAdd(counters + 1, 1ull);
+    }
+}
+
+// state <- snapshot; when check >= 0 only if that check flagged drift.
+template <typename C2>
+__global__ void restore_kernel(C2 *state, const C2 *snap, uint64_t dim, const int *restore_flag,
+                               int check) {
+    if (check >= 0 && !restore_flag[check]) return;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        state[i] = snap[i];
+}
+
+// ------------------------------------------------------------ host launchers
+
+template <typename R, int V>
+static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
+    size_t smem = (sizeof(R) * 2) << a.d.L;
+    const int threads = 1 << (a.d.L - V);
+    auto k = pass_kernel<R, V>;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured = true;
+    }
+    k<<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st) {
+    if (precision == TUSQ_C128) {
+        switch (V) {
+        case 1: return launch_pass_t<double, 1>(a, grid, st);
+        case 2: return launch_pass_t<double, 2>(a, grid, st);
+        case 3: return launch_pass_t<double, 3>(a, grid, st);
+        default: return launch_pass_t<double, 4>(a, grid, st);
+        }
+    }
+    switch (V) {
+    case 1: return launch_pass_t<float, 1>(a, grid, st);
+    case 2: return launch_pass_t<float, 2>(a, grid, st);
+    case 3: return launch_pass_t<float, 3>(a, grid, st);
+    case 4: return launch_pass_t<float, 4>(a, grid, st);
+    default: return launch_pass_t<float, 5>(a, grid, st);
+    }
+}
+
+// Resident CTAs per SM for a pass configuration (for grid sizing).
+int pass_occupancy(int precision, int V, int L) {
+    size_t smem = (precision == TUSQ_C128 ? 16 : 8) << L;
+    const int threads = 1 << (L - V);
+    int nb = 0;
+    cudaError_t e;
+    if (precision == TUSQ_C128) {
+        switch (V) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 1>, threads, smem); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 2>, threads, smem); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 3>, threads, smem); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 4>, threads, smem); break;
+        }
+    } else {
+        switch (V) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 1>, threads, smem); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 2>, threads, smem); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 3>, threads, smem); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 4>, threads, smem); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 5>, threads, smem); break;
+        }
+    }
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st) {
+    int grid = (int)((dim + 255) / 256);
+    if (grid > nsm * 8) grid = nsm * 8;
+    if (precision == TUSQ_C128) init_kernel<double2><<<grid, 256, 0, st>>>((double2 *)state, dim);
+    else init_kernel<float2><<<grid, 256, 0, st>>>((float2 *)state, dim);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
+                            int is_check, double *drift_log, int check, int *restore_flag,
+                            int has_snapshot, double tol, unsigned long long *counters,
+                            double record_bias, cudaStream_t st) {
+    finalize_kernel<<<1, 32, 0, st>>>(partials, nparts, records, depth, is_check, drift_log, check,
+                                      restore_flag, has_snapshot, tol, counters, record_bias);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore(void *state, const void *snap, int precision, uint64_t dim,
+                           const int *restore_flag, int check, int nsm, cudaStream_t st) {
+    int grid = (int)((dim + 255) / 256);
+    if (grid > nsm * 8) grid = nsm * 8;
+    if (precision == TUSQ_C128)
+        restore_kernel<double2><<<grid, 256, 0, st>>>((double2 *)state, (const double2 *)snap, dim,
+                                                      restore_flag, check);
+    else
+        restore_kernel<float2><<<grid, 256, 0, st>>>((float2 *)state, (const float2 *)snap, dim,
+                                                     restore_flag, check);
+    return cudaGetLastError();
+}
+
+}  // namespace tusq

@@ -1,0 +1,127 @@
+// Device program of one DFTT traversal: the layout shared by the schedule
+// compiler (host C++) and the CUDA kernels/runtime.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tusq.h"
+
+namespace tusq {
+
+constexpr int kMaxTileBits = 14;     // a pass tile holds at most 2^14 amplitudes
+constexpr int kMaxStages = 8;        // register stages per pass
+constexpr int kRegBitsC64 = 5;       // amplitudes per thread = 2^5 (complex64)
+constexpr int kRegBitsC128 = 4;      // 2^4 (complex128)
+
+enum DevOpType : int32_t { OP_MAT1 = 1, OP_MAT2 = 2, OP_DIAG = 3 };
+
+// One operation of a stage, on the register bits of that stage.
+//   MAT1: 2x2 on register bit a (row-major, basis bit a).
+//   MAT2: 4x4 on register bits a < b, basis index bit_a + 2*bit_b.
+//   DIAG: amp(x) *= exp(2 pi i (phi0 + sum_k phi_k parity(x & mask_k))) with
+//         x the global index; phases in fixed point (2^-31 turn units for
+//         complex64, 2^-63 for complex128); terms sorted by their mask
+//         restricted to the register bits (mu), csr[mu]..csr[mu+1].
+struct DevOp {
+    int32_t type;
+    int32_t a, b;
+    uint32_t mat;          // index of the 4x4 slot in the matrix pools
+    uint32_t term_begin;   // DIAG: first term
+    uint32_t pad0;
+    uint64_t phi0;         // DIAG: constant phase (fixed point)
+    uint16_t csr[34];      // DIAG: term offsets per register mask mu (relative)
+    uint32_t pad1[3];
+};
+static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
+
+struct StageDesc {
+    uint8_t rbits[8];      // local bit positions held in registers (ascending)
+    uint8_t cpos[16];      // remaining local bit positions (ascending) -> thread bits
+    uint16_t sr[32];       // swizzled shared-memory offset of register index r
+    uint64_t greg[8];      // global bit of each register bit (1 << win[rbits[i]])
+    uint32_t op_begin, op_count;
+};
+
+enum PassFlags : uint32_t {
+    PF_WRITE = 1,          // write the tile back to the state
+    PF_SNAPSHOT = 2,       // also write it to the snapshot buffer
+    PF_LEAF = 4,           // acc[x] += w |psi_x|^2
+    PF_REDUCE = 8,         // partial sums of |psi|^2 and sum h(x) psi_x
+};
+
+struct PassDesc {
+    int32_t L;             // tile = 2^L amplitudes
+    int32_t n_stages;
+    int32_t n_cw;          // number of tile-index bits
+    uint32_t flags;
+    uint64_t ntiles;
+    uint8_t win[16];       // local bit i <-> global bit win[i]
+    uint8_t cw[40];        // global positions of the tile-index bits (ascending)
+    uint64_t grow[32];     // global offset of load row i (local index i * T)
+    uint16_t srow[32];     // swizzled shared offset of load row i
+    StageDesc st[kMaxStages];
+    double leaf_w;
+    int32_t snap;          // snapshot slot for PF_SNAPSHOT
+    int32_t pad;
+};
+
+// Host-side step of the traversal.
+enum StepType : int32_t {
+    ST_INIT = 1,           // state <- |0..0>
+    ST_PASS = 2,           // fused pass (PassDesc index)
+    ST_RECORD = 3,         // partial sums -> record[depth]
+    ST_CHECK = 4,          // partial sums vs record[depth] -> drift log; flag restore
+    ST_RESTORE = 5,        // if flagged: state <- snapshot[snap]
+};
+
+struct Step {
+    int32_t type;
+    int32_t pass;          // ST_PASS
+    int32_t depth;         // ST_RECORD / ST_CHECK
+    int32_t snap;          // ST_CHECK / ST_RESTORE (-1: none)
+    int32_t check;         // index into the drift log
+};
+
+struct Program {
+    int n = 0;
+    int precision = 0;
+    int reg_bits = 5;
+    std::vector<Step> steps;
+    std::vector<PassDesc> passes;
+    std::vector<DevOp> ops;
+    std::vector<double> mats;        // 32 doubles (16 complex) per matrix slot
+    std::vector<uint64_t> term_mask;
+    std::vector<uint64_t> term_phi;
+    int max_depth = 0;
+    int n_checks = 0;
+    int n_snapshots = 0;
+    // counters
+    uint64_t gate_apps = 0, pauli_apps = 0, passes_count = 0, leaf_passes = 0, resets = 0;
+    uint64_t restores = 0;           // unconditional snapshot restores (snapshot policy)
+};
+
+// Arguments of one pass launch.
+struct PassArgs {
+    PassDesc d;
+    void *state;
+    void *snap;           // snapshot buffer for PF_SNAPSHOT
+    double *acc;          // FP64 output for PF_LEAF
+    double *partials;     // 3 doubles per CTA for PF_REDUCE
+    const DevOp *ops;
+    const double *mats;
+    const uint64_t *tmask;
+    const uint64_t *tphi;
+};
+
+struct CompileOpts {
+    int precision;
+    int max_window;
+    int traversal;
+    int leaf_peek;
+    int root_reset;
+    bool checks;
+    int snapshots;         // snapshot slots available
+};
+
+}  // namespace tusq

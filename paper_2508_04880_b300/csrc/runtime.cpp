@@ -1,0 +1,471 @@
+// Host runtime of the DFTT engine: compiles a plan into a device program,
+// owns the device buffers (state, LIFO snapshot pool, check records) and
+// enqueues the traversal on a CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+#include "program.h"
+
+namespace tusq {
+
+void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
+
+cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st);
+int pass_occupancy(int precision, int V, int L);
+cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st);
+cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
+                            int is_check, double *drift_log, int check, int *restore_flag,
+                            int has_snapshot, double tol, unsigned long long *counters,
+                            double record_bias, cudaStream_t st);
+cudaError_t launch_restore(void *state, const void *snap, int precision, uint64_t dim,
+                           const int *restore_flag, int check, int nsm, cudaStream_t st);
+
+}  // namespace tusq
+
+using namespace tusq;
+
+struct tusq_exec {
+    Program prog;
+    tusq_run_opts opts{};
+    int n = 0;
+    uint64_t dim = 0;
+    size_t amp_bytes = 8;
+    int nsm = 148;
+    int V = 5;
+    cudaStream_t stream = nullptr;
+    // device buffers
+    void *state = nullptr;
+    void *snaps = nullptr;
+    int n_snaps = 0;
+    double *records = nullptr;
+    double *partials = nullptr;
+    double *drift_log = nullptr;
+    int *restore_flag = nullptr;
+    unsigned long long *counters = nullptr;
+    DevOp *ops = nullptr;
+    double *mats = nullptr;
+    uint64_t *tmask = nullptr, *tphi = nullptr;
+    std::vector<int> grid_of_pass;
+    int max_grid = 1;
+    double record_bias = 0.0;
+    uint64_t launches = 0;
+    size_t footprint = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<float> prof_ms;
+    std::vector<double> prof_bytes;
+};
+
+namespace {
+
+#define CUDA_TRY(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return TUSQ_ECUDA;                                                      \
+        }                                                                           \
+    } while (0)
+
+template <class T>
+int dmalloc(T **p, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, st);
+    if (e != cudaSuccess) {
+        set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                  cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TUSQ_ENOMEM : TUSQ_ECUDA;
+    }
+    return TUSQ_OK;
+}
+
+void release(tusq_exec *e) {
+    void *bufs[] = {e->state, e->snaps, e->records, e->partials, e->drift_log, e->restore_flag,
+                    e->counters, e->ops, e->mats, e->tmask, e->tphi};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, e->stream);
+    e->state = e->snaps = nullptr;
+    e->records = e->partials = e->drift_log = nullptr;
+    e->restore_flag = nullptr;
+    e->counters = nullptr;
+    e->ops = nullptr;
+    e->mats = nullptr;
+    e->tmask = e->tphi = nullptr;
+}
+
+}  // namespace
+
+namespace tusq {
+
+static CompileOpts compile_opts_of(const tusq_run_opts *o, size_t state_bytes) {
+    CompileOpts co;
+    co.precision = o->precision;
+    co.max_window = o->max_window;
+    co.traversal = o->traversal;
+    co.leaf_peek = o->leaf_peek;
+    co.root_reset = o->root_reset;
+    co.checks = o->drift_tol >= 0 && o->traversal != TUSQ_FROM_SCRATCH;
+    bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
+    co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
+    return co;
+}
+
+// Algorithmic HBM bytes of one pass: the state read, its write (and the
+// snapshot write) when asked, and the FP64 accumulator read + write of a
+// leaf pass.
+static double pass_bytes(const PassDesc &d, double state_bytes, uint64_t dim) {
+    double b = state_bytes;
+    if (d.flags & PF_WRITE) b += state_bytes;
+    if (d.flags & PF_SNAPSHOT) b += state_bytes;
+    if (d.flags & PF_LEAF) b += 16.0 * dim;
+    return b;
+}
+
+// What a launch of the program executes, known on the host.
+static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_run_info_t *info) {
+    std::memset(info, 0, sizeof *info);
+    info->passes = pg.passes_count;
+    info->gate_apps = pg.gate_apps;
+    info->pauli_apps = pg.pauli_apps;
+    info->leaf_passes = pg.leaf_passes;
+    info->checks = pg.n_checks;
+    info->resets = pg.resets;
+    info->restores = pg.restores;
+    info->state_bytes = (double)(amp_bytes * dim);
+    // every pass reads the state and writes it (and a snapshot) when asked;
+    // a leaf pass also reads and writes the FP64 accumulator; a reset
+    // writes the state; an unconditional restore copies a snapshot
+    const double sb = info->state_bytes;
+    double bytes = 0;
+    uint64_t launches = 0;
+    for (const Step &s : pg.steps) {
+        ++launches;
+        if (s.type == ST_PASS) {
+            bytes += pass_bytes(pg.passes[s.pass], sb, dim);
+        } else if (s.type == ST_INIT) {
+            bytes += sb;
+        } else if (s.type == ST_RESTORE && s.check < 0) {
+            bytes += 2 * sb;
+        }
+    }
+    info->kernel_launches = launches;
+    info->algorithmic_bytes = bytes;
+    info->program_bytes = (double)(sizeof(DevOp) * pg.ops.size() + sizeof(double) * pg.mats.size() +
+                                   sizeof(uint64_t) * (pg.term_mask.size() + pg.term_phi.size()));
+}
+
+// Device bytes an exec of this plan needs (state + snapshots + program).
+size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
+    size_t amp = o->precision == TUSQ_C128 ? 16 : 8;
+    size_t state = amp << p->n;
+    CompileOpts co = compile_opts_of(o, state);
+    return state * (1 + co.snapshots) + (1u << 20);
+}
+
+int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t *info) {
+    size_t amp = o->precision == TUSQ_C128 ? 16 : 8;
+    Program pg;
+    try {
+        compile_program(*p, compile_opts_of(o, amp << p->n), pg);
+    } catch (const std::exception &ex) {
+        set_error(std::string("tusq_compile_stats: schedule compilation failed: ") + ex.what());
+        return TUSQ_EINVAL;
+    }
+    static_info(pg, amp, 1ULL << p->n, info);
+    return TUSQ_OK;
+}
+
+int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out) {
+    tusq_exec *e = new (std::nothrow) tusq_exec;
+    if (!e) { set_error("tusq_exec_create: out of host memory"); return TUSQ_ENOMEM; }
+    e->opts = *o;
+    e->n = p->n;
+    e->dim = 1ULL << p->n;
+    e->amp_bytes = o->precision == TUSQ_C128 ? 16 : 8;
+    e->stream = st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e->nsm <= 0) e->nsm = 148;
+    const size_t state_bytes = e->amp_bytes * e->dim;
+    CompileOpts co = compile_opts_of(o, state_bytes);
+    try {
+        compile_program(*p, co, e->prog);
+    } catch (const std::exception &ex) {
+        delete e;
+        set_error(std::string("tusq_exec_create: schedule compilation failed: ") + ex.what());
+        return TUSQ_EINVAL;
+    }
+    Program &pg = e->prog;
+    e->V = pg.reg_bits;
+    e->n_snaps = std::min(co.snapshots, pg.max_depth);
+    // grid of every pass
+    e->grid_of_pass.resize(pg.passes.size());
+    int occ_cache[2][16] = {{0}};
+    for (size_t i = 0; i < pg.passes.size(); ++i) {
+        const PassDesc &d = pg.passes[i];
+        int V = std::min(e->V, d.L);
+        int &occ = occ_cache[0][d.L];
+        if (!occ) occ = pass_occupancy(o->precision, V, d.L);
+        uint64_t g = std::min<uint64_t>(d.ntiles, (uint64_t)e->nsm * occ);
+        e->grid_of_pass[i] = (int)std::max<uint64_t>(g, 1);
+        e->max_grid = std::max(e->max_grid, e->grid_of_pass[i]);
+    }
+    int rc;
+#define ALLOC(ptr, bytes) \
+    if ((rc = dmalloc(&(ptr), (bytes), st)) != TUSQ_OK) { release(e); delete e; return rc; }
+    ALLOC(e->state, state_bytes);
+    if (e->n_snaps > 0) ALLOC(e->snaps, state_bytes * e->n_snaps);
+    ALLOC(e->records, sizeof(double) * 4 * std::max(pg.max_depth, 1));
+    ALLOC(e->partials, sizeof(double) * 3 * e->max_grid);
+    ALLOC(e->drift_log, sizeof(double) * std::max(pg.n_checks, 1));
+    ALLOC(e->restore_flag, sizeof(int) * std::max(pg.n_checks, 1));
+    ALLOC(e->counters, sizeof(unsigned long long) * 4);
+    ALLOC(e->ops, sizeof(DevOp) * std::max<size_t>(pg.ops.size(), 1));
+    ALLOC(e->mats, sizeof(double) * std::max<size_t>(pg.mats.size(), 1));
+    ALLOC(e->tmask, sizeof(uint64_t) * std::max<size_t>(pg.term_mask.size(), 1));
+    ALLOC(e->tphi, sizeof(uint64_t) * std::max<size_t>(pg.term_phi.size(), 1));
+#undef ALLOC
+    auto up = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (!bytes) return TUSQ_OK;
+        cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); return TUSQ_ECUDA; }
+        return TUSQ_OK;
+    };
+    if ((rc = up(e->ops, pg.ops.data(), sizeof(DevOp) * pg.ops.size())) ||
+        (rc = up(e->mats, pg.mats.data(), sizeof(double) * pg.mats.size())) ||
+        (rc = up(e->tmask, pg.term_mask.data(), sizeof(uint64_t) * pg.term_mask.size())) ||
+        (rc = up(e->tphi, pg.term_phi.data(), sizeof(uint64_t) * pg.term_phi.size()))) {
+        release(e);
+        delete e;
+        return rc;
+    }
+    // the host program arrays are consumed by the asynchronous copies
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+        release(e);
+        delete e;
+        set_error(std::string("tusq_exec_create: ") + cudaGetErrorString(ce));
+        return TUSQ_ECUDA;
+    }
+    e->footprint = state_bytes * (1 + e->n_snaps);
+    *out = e;
+    return TUSQ_OK;
+}
+
+int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
+    Program &pg = e->prog;
+    e->stream = st;
+    e->launches = 0;
+    CUDA_TRY(cudaMemsetAsync(probs, 0, sizeof(double) * e->dim, st));
+    CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(unsigned long long) * 4, st));
+    if (pg.n_checks) {
+        CUDA_TRY(cudaMemsetAsync(e->drift_log, 0, sizeof(double) * pg.n_checks, st));
+        CUDA_TRY(cudaMemsetAsync(e->restore_flag, 0, sizeof(int) * pg.n_checks, st));
+    }
+    const size_t state_bytes = e->amp_bytes * e->dim;
+    int last_grid = 1;
+    size_t npass = 0;
+    if (e->profiling) {
+        size_t np = 0;
+        for (const Step &s : pg.steps) np += (s.type == ST_PASS);
+        while (e->prof_ev.size() < 2 * np) {
+            cudaEvent_t ev;
+            CUDA_TRY(cudaEventCreate(&ev));
+            e->prof_ev.push_back(ev);
+        }
+        e->prof_bytes.assign(np, 0.0);
+        e->prof_ms.assign(np, 0.f);
+    }
+    for (const Step &s : pg.steps) {
+        switch (s.type) {
+        case ST_INIT:
+            CUDA_TRY(launch_init(e->state, e->opts.precision, e->dim, e->nsm, st));
+            e->launches++;
+            break;
+        case ST_PASS: {
+            PassArgs a;
+            a.d = pg.passes[s.pass];
+            a.state = e->state;
+            a.snap = (a.d.flags & PF_SNAPSHOT) ? (char *)e->snaps + state_bytes * a.d.snap : nullptr;
+            a.acc = probs;
+            a.partials = e->partials;
+            a.ops = e->ops;
+            a.mats = e->mats;
+            a.tmask = e->tmask;
+            a.tphi = e->tphi;
+            last_grid = e->grid_of_pass[s.pass];
+            if (e->profiling) CUDA_TRY(cudaEventRecord(e->prof_ev[2 * npass], st));
+            CUDA_TRY(launch_pass(a, e->opts.precision, std::min(e->V, a.d.L), last_grid, st));
+            if (e->profiling) {
+                CUDA_TRY(cudaEventRecord(e->prof_ev[2 * npass + 1], st));
+                e->prof_bytes[npass] = pass_bytes(a.d, e->amp_bytes * e->dim, e->dim);
+            }
+            ++npass;
+            e->launches++;
+            break;
+        }
+        case ST_RECORD:
+            CUDA_TRY(launch_finalize(e->partials, last_grid, e->records, s.depth, 0, e->drift_log, 0,
+                                     e->restore_flag, 0, e->opts.drift_tol, e->counters,
+                                     e->record_bias, st));
+            e->launches++;
+            break;
+        case ST_CHECK:
+            CUDA_TRY(launch_finalize(e->partials, last_grid, e->records, s.depth, 1, e->drift_log,
+                                     s.check, e->restore_flag, s.snap >= 0 ? 1 : 0,
+                                     e->opts.drift_tol, e->counters, 0.0, st));
+            e->launches++;
+            break;
+        case ST_RESTORE:
+            CUDA_TRY(launch_restore(e->state, (char *)e->snaps + state_bytes * s.snap,
+                                    e->opts.precision, e->dim, e->restore_flag, s.check, e->nsm, st));
+            e->launches++;
+            break;
+        default:
+            set_error("exec_launch: bad step");
+            return TUSQ_EINVAL;
+        }
+    }
+    return TUSQ_OK;
+}
+
+int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
+    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    unsigned long long cnt[4] = {0};
+    CUDA_TRY(cudaMemcpy(cnt, e->counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    double maxd = 0;
+    if (e->prog.n_checks) {
+        std::vector<double> log(e->prog.n_checks);
+        CUDA_TRY(cudaMemcpy(log.data(), e->drift_log, sizeof(double) * log.size(),
+                            cudaMemcpyDeviceToHost));
+        for (double v : log) maxd = std::max(maxd, v);
+    }
+    if (e->profiling)
+        for (size_t i = 0; i < e->prof_ms.size(); ++i)
+            CUDA_TRY(cudaEventElapsedTime(&e->prof_ms[i], e->prof_ev[2 * i], e->prof_ev[2 * i + 1]));
+    if (info) {
+        static_info(e->prog, e->amp_bytes, e->dim, info);
+        info->restores += cnt[0];
+        info->unrecovered = cnt[1];
+        info->kernel_launches = e->launches;
+        info->max_drift = maxd;
+    }
+    if (cnt[1]) {
+        set_error("drift above tolerance at a branch node without a snapshot");
+        return TUSQ_EDRIFT;
+    }
+    return TUSQ_OK;
+}
+
+void exec_free(tusq_exec *e) {
+    if (!e) return;
+    for (cudaEvent_t ev : e->prof_ev) cudaEventDestroy(ev);
+    release(e);
+    cudaStreamSynchronize(e->stream);
+    delete e;
+}
+
+}  // namespace tusq
+
+extern "C" {
+
+void tusq_run_opts_default(tusq_run_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = TUSQ_C64;
+    o->max_window = 0;
+    o->traversal = TUSQ_DFTT;
+    o->leaf_peek = 1;
+    o->root_reset = 1;
+    o->drift_tol = 1e-6;
+    o->snapshot_bytes = 0;      // 0 -> 8 states (resolved in tusq_exec_create)
+    o->check_every = 0;
+}
+
+// Validate and complete run options (0 snapshot bytes -> 8 states).
+static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run_opts &o,
+                        const char *who) {
+    tusq_run_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != TUSQ_C64 && o.precision != TUSQ_C128) {
+        set_error(std::string(who) + ": bad precision");
+        return TUSQ_EINVAL;
+    }
+    if (o.traversal < TUSQ_DFTT || o.traversal > TUSQ_DFTT_SNAPSHOT) {
+        set_error(std::string(who) + ": bad traversal");
+        return TUSQ_EINVAL;
+    }
+    if (o.max_window < 0 || o.max_window > kMaxTileBits) {
+        set_error(std::string(who) + ": max_window must be in [0, 14]");
+        return TUSQ_EINVAL;
+    }
+    if (o.snapshot_bytes == 0) o.snapshot_bytes = (uint64_t)8 * ((uint64_t)(o.precision == TUSQ_C128 ? 16 : 8) << p->n);
+    return TUSQ_OK;
+}
+
+int tusq_exec_create(const tusq_plan_t *p, const tusq_run_opts *opts, void *cuda_stream,
+                     tusq_exec **out) {
+    if (!p || !out) { set_error("tusq_exec_create: NULL argument"); return TUSQ_EINVAL; }
+    tusq_run_opts o;
+    int rc = resolve_opts(p, opts, o, "tusq_exec_create");
+    if (rc) return rc;
+    return exec_create(p, &o, (cudaStream_t)cuda_stream, out);
+}
+
+int tusq_compile_stats(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run_info_t *out) {
+    if (!p || !out) { set_error("tusq_compile_stats: NULL argument"); return TUSQ_EINVAL; }
+    tusq_run_opts o;
+    int rc = resolve_opts(p, opts, o, "tusq_compile_stats");
+    if (rc) return rc;
+    return compile_stats(p, &o, out);
+}
+
+int tusq_exec_launch(tusq_exec *e, double *probs_dev, void *cuda_stream) {
+    if (!e || !probs_dev) { set_error("tusq_exec_launch: NULL argument"); return TUSQ_EINVAL; }
+    return exec_launch(e, probs_dev, (cudaStream_t)cuda_stream);
+}
+
+int tusq_exec_finish(tusq_exec *e, tusq_run_info_t *info) {
+    if (!e) { set_error("tusq_exec_finish: NULL exec"); return TUSQ_EINVAL; }
+    return exec_finish(e, info);
+}
+
+int tusq_exec_set_profiling(tusq_exec *e, int on) {
+    if (!e) { set_error("tusq_exec_set_profiling: NULL exec"); return TUSQ_EINVAL; }
+    e->profiling = on != 0;
+    return TUSQ_OK;
+}
+
+int tusq_exec_pass_profile(tusq_exec *e, uint64_t *n_passes, const float **ms, const double **bytes) {
+    if (!e || !n_passes) { set_error("tusq_exec_pass_profile: NULL argument"); return TUSQ_EINVAL; }
+    *n_passes = e->prof_ms.size();
+    if (ms) *ms = e->prof_ms.data();
+    if (bytes) *bytes = e->prof_bytes.data();
+    return TUSQ_OK;
+}
+
+int tusq_exec_set_record_bias(tusq_exec *e, double delta) {
+    if (!e) { set_error("tusq_exec_set_record_bias: NULL exec"); return TUSQ_EINVAL; }
+    e->record_bias = delta;
+    return TUSQ_OK;
+}
+
+void tusq_exec_free(tusq_exec *e) { exec_free(e); }
+
+int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev, void *cuda_stream) {
+    tusq_exec *e = nullptr;
+    int rc = tusq_exec_create(p, opts, cuda_stream, &e);
+    if (rc) return rc;
+    rc = tusq_exec_launch(e, probs_dev, cuda_stream);
+    if (rc == TUSQ_OK) rc = tusq_exec_finish(e, nullptr);
+    tusq_exec_free(e);
+    return rc;
+}
+
+}  // extern "C"

@@ -171,6 +171,16 @@ int tusq_plan_export_tally(const tusq_plan_t *p, int stage, uint64_t *n, const u
                            const int32_t **a, const int32_t **b, const int32_t **c,
                            const uint64_t **counts);
 
+/* Subtree sharding for several GPUs (the parallel-subtree form of DFTT,
+ * Sec. III-B): the DFS-ordered instances are cut into `world` contiguous
+ * chunks of nearly equal estimated work (each chunk is a set of subtrees
+ * plus the path to them); *out gets chunk `rank` as its own plan with the
+ * original weights, so the sum over ranks of the ranks' output
+ * distributions is the full one -- the only exchange is that FP64
+ * sum-reduce, done by the caller.  An empty chunk (world > N) is a plan
+ * with no instances. */
+int tusq_plan_shard(const tusq_plan_t *p, int rank, int world, tusq_plan_t **out);
+
 int tusq_plan_n_qubits(const tusq_plan_t *p);
 void tusq_plan_free(tusq_plan_t *p);
 

@@ -32,7 +32,8 @@ EXPORTS = [
     "tusq_circuit_create", "tusq_circuit_add_gate", "tusq_circuit_set_channel", "tusq_circuit_free",
     "tusq_plan", "tusq_plan_stats", "tusq_plan_from_instances", "tusq_plan_export",
     "tusq_plan_export_tally",
-    "tusq_plan_n_qubits", "tusq_plan_free", "tusq_run_opts_default", "tusq_exec_create",
+    "tusq_plan_n_qubits", "tusq_plan_shard", "tusq_plan_free", "tusq_run_opts_default",
+    "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_free",
     "tusq_run", "tusq_server_create", "tusq_submit", "tusq_poll", "tusq_server_drain",
@@ -101,6 +102,7 @@ def _load():
         "tusq_plan_export_tally": (i32, [vp, i32, P(u64), P(P(u64)), P(P(ctypes.c_int32)),
                                          P(P(ctypes.c_int32)), P(P(ctypes.c_int32)), P(P(u64))]),
         "tusq_plan_n_qubits": (i32, [vp]),
+        "tusq_plan_shard": (i32, [vp, i32, i32, P(vp)]),
         "tusq_plan_free": (None, [vp]),
         "tusq_run_opts_default": (None, [P(RunOpts)]),
         "tusq_exec_create": (i32, [vp, P(RunOpts), vp, P(vp)]),
@@ -196,6 +198,13 @@ class Plan:
         if getattr(self, "h", None):
             lib.tusq_plan_free(self.h)
             self.h = None
+
+    def shard(self, rank: int, world: int) -> "Plan":
+        """Contiguous DFS chunk `rank` of `world` (subtree sharding); the
+        ranks' output distributions sum to this plan's."""
+        h = ctypes.c_void_p()
+        _check(lib.tusq_plan_shard(self.h, rank, world, ctypes.byref(h)))
+        return Plan(h, self.n_qubits)
 
     def stats(self) -> dict:
         s = PlanStats()

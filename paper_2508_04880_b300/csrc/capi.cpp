@@ -13,6 +13,7 @@ int build_plan(const tusq_circuit &circ, const tusq_plan_opts &opts, uint64_t sh
 int build_plan_from_instances(const tusq_circuit &circ, uint64_t n_inst, const uint64_t *ev_off,
                               const int32_t *ev_slot, const int32_t *ev_qubit,
                               const int32_t *ev_pauli, const double *weights, tusq_plan_t &P);
+int build_plan_shard(const tusq_plan_t &src, int rank, int world, tusq_plan_t &P);
 
 static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
@@ -198,6 +199,21 @@ int tusq_plan_export_tally(const tusq_plan_t *p, int stage, uint64_t *n, const u
     if (b) *b = L.b.data();
     if (c) *c = L.c.data();
     if (counts) *counts = L.count.data();
+    return TUSQ_OK;
+}
+
+int tusq_plan_shard(const tusq_plan_t *p, int rank, int world, tusq_plan_t **out) {
+    if (!p || !out) TUSQ_FAIL(TUSQ_EINVAL, "tusq_plan_shard: NULL argument");
+    if (world < 1 || rank < 0 || rank >= world) TUSQ_FAIL(TUSQ_EINVAL, "tusq_plan_shard: bad rank/world");
+    tusq_plan_t *s = new (std::nothrow) tusq_plan_t;
+    if (!s) TUSQ_FAIL(TUSQ_ENOMEM, "tusq_plan_shard: out of host memory");
+    try {
+        build_plan_shard(*p, rank, world, *s);
+    } catch (const std::bad_alloc &) {
+        delete s;
+        TUSQ_FAIL(TUSQ_ENOMEM, "tusq_plan_shard: out of host memory");
+    }
+    *out = s;
     return TUSQ_OK;
 }
 

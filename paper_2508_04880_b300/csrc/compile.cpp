@@ -28,6 +28,7 @@ struct HOp {
     bool pauli = false;
     int key = 0;                  // canonical position: 2*slot for events, 2*slot+1 for gates
     int uid = 0;                  // identity within the instance (for set differences)
+    std::vector<int> merged;      // uids of ops merged into this one (besides uid)
     cd m[16];
     double phi0 = 0;              // DIAG, in turns
     std::vector<std::pair<uint64_t, double>> terms;   // (global mask, turns)
@@ -194,6 +195,11 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
 // qubit inside one op list (application order).
 std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
     std::vector<HOp> out;
+    auto absorb = [](HOp &p, const HOp &o) {
+        p.merged.push_back(o.uid);
+        p.merged.insert(p.merged.end(), o.merged.begin(), o.merged.end());
+        p.pauli = false;
+    };
     for (const HOp &o : in) {
         if (!out.empty()) {
             HOp &p = out.back();
@@ -205,7 +211,7 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
                         if (u.first == t.first) { u.second += t.second; hit = true; break; }
                     if (!hit) p.terms.push_back(t);
                 }
-                p.pauli = false;
+                absorb(p, o);
                 continue;
             }
             if (o.type == H_MAT1 && p.type == H_MAT1 && o.q0 == p.q0) {
@@ -214,7 +220,7 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
                     for (int k = 0; k < 2; ++k)
                         r[2 * i + k] = o.m[2 * i] * p.m[k] + o.m[2 * i + 1] * p.m[2 + k];
                 for (int k = 0; k < 4; ++k) p.m[k] = r[k];
-                p.pauli = false;
+                absorb(p, o);
                 continue;
             }
         }
@@ -247,9 +253,12 @@ struct Encoder {
     int Lmax;
 
     // Encode one pass (window + ops already in application order) into
-    // PassDescs (several if the register stages exceed kMaxStages).
+    // PassDescs (several if the register stages exceed kMaxStages; only the
+    // last one carries `flags`).  last_uids receives the uids of the ops in
+    // that last PassDesc.
     void emit(const std::vector<int> &win, const std::vector<HOp> &ops_in, uint32_t flags,
-              double leaf_w, int snap, std::vector<int> &pass_ids) {
+              double leaf_w, int snap, std::vector<int> &pass_ids, std::vector<int> *last_uids) {
+        if (last_uids) last_uids->clear();
         const int L = (int)win.size();
         int local[64];
         for (int i = 0; i < 64; ++i) local[i] = -1;
@@ -315,6 +324,10 @@ struct Encoder {
                 sd.op_begin = (uint32_t)prog.ops.size();
                 for (int oi : stages[s]) {
                     const HOp &o = ops[oi];
+                    if (last && last_uids) {
+                        last_uids->push_back(o.uid);
+                        last_uids->insert(last_uids->end(), o.merged.begin(), o.merged.end());
+                    }
                     DevOp d;
                     std::memset(&d, 0, sizeof d);
                     if (o.type == H_MAT1) {
@@ -439,10 +452,10 @@ struct Compiler {
         for (int id : ids) prog.steps.push_back(Step{ST_PASS, id, 0, -1, 0});
     }
 
-    // Schedule a list of ops into passes; the last pass gets `last_flags`.
-    // Returns the ops of the last pass (application order) through last_ops.
+    // Schedule a list of ops into passes; the last launch gets `last_flags`.
+    // last_uids receives the uids of the ops applied by that last launch.
     void emit_ops(const std::vector<HOp> &ops, uint32_t last_flags, double w, int snap,
-                  std::vector<HOp> *last_ops) {
+                  std::vector<int> *last_uids) {
         count(ops);
         std::vector<uint64_t> wins;
         auto gq = [](const HOp &o) { return o.type == H_DIAG ? 0ULL : o.qmask(); };
@@ -453,9 +466,8 @@ struct Compiler {
             std::vector<int> win;
             for (int b = 0; b < L; ++b) win.push_back(b);
             std::vector<int> ids;
-            enc.emit(win, {}, last_flags, w, snap, ids);
+            enc.emit(win, {}, last_flags, w, snap, ids, last_uids);
             push_passes(ids);
-            if (last_ops) last_ops->clear();
             return;
         }
         for (size_t gi = 0; gi < groups.size(); ++gi) {
@@ -468,9 +480,8 @@ struct Compiler {
             for (int oi : groups[gi]) pops.push_back(ops[oi]);
             bool last = (gi + 1 == groups.size());
             std::vector<int> ids;
-            enc.emit(win, pops, last ? last_flags : PF_WRITE, w, snap, ids);
+            enc.emit(win, pops, last ? last_flags : PF_WRITE, w, snap, ids, last ? last_uids : nullptr);
             push_passes(ids);
-            if (last && last_ops) *last_ops = pops;
         }
     }
 
@@ -516,7 +527,7 @@ struct Compiler {
             bounds.push_back(t_in);
             for (int s : chain) if (s > bounds.back()) bounds.push_back(s);
             bounds.push_back(G + 1);
-            std::vector<HOp> leaf_ops;
+            std::vector<int> leaf_ops;     // uids the unwritten leaf launch applied
             bool last_inst = (i + 1 == N);
             for (size_t s = 0; s + 1 < bounds.size(); ++s) {
                 std::vector<HOp> ops = segment(i, bounds[s], bounds[s + 1]);
@@ -559,7 +570,7 @@ struct Compiler {
     }
 
     template <class Stack>
-    void return_to(uint64_t i, int t, const std::vector<HOp> &leaf_ops, Stack &stack, bool snap_policy) {
+    void return_to(uint64_t i, int t, const std::vector<int> &leaf_ops, Stack &stack, bool snap_policy) {
             const int G = this->G;
             if (snap_policy && !stack.empty() && stack.back().snap >= 0) {
                 // the branch node's own snapshot: one copy pass back to it
@@ -573,8 +584,8 @@ struct Compiler {
             std::vector<HOp> undo;
             for (auto it = all.rbegin(); it != all.rend(); ++it) {
                 bool skipped = false;
-                for (auto &lo : leaf_ops)
-                    if (lo.uid == it->uid) { skipped = true; break; }
+                for (int u : leaf_ops)
+                    if (u == it->uid) { skipped = true; break; }
                 if (!skipped) undo.push_back(inverse(*it));
             }
             if (undo.empty()) return;     // the state never left the branch node

@@ -367,18 +367,37 @@ __global__ void restore_kernel(C2 *state, const C2 *snap, uint64_t dim, const in
 
 // ------------------------------------------------------------ host launchers
 
+// Allow the dynamic shared memory a pass tile needs (above the 48 KB
+// default); returns the attribute call's own status.
+template <typename R, int V>
+static cudaError_t allow_smem(size_t smem) {
+    static size_t allowed = 48 * 1024;
+    if (smem <= allowed) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) allowed = smem;
+    return e;
+}
+
 template <typename R, int V>
 static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
-    size_t smem = (sizeof(R) * 2) << a.d.L;
+    const size_t smem = (sizeof(R) * 2) << a.d.L;
     const int threads = 1 << (a.d.L - V);
-    auto k = pass_kernel<R, V>;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        configured = true;
-    }
-    k<<<grid, threads, smem, st>>>(a);
+    cudaError_t e = allow_smem<R, V>(smem);
+    if (e != cudaSuccess) return e;
+    pass_kernel<R, V><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename R, int V>
+static int occupancy_t(int L) {
+    const size_t smem = (sizeof(R) * 2) << L;
+    const int threads = 1 << (L - V);
+    int nb = 0;
+    if (allow_smem<R, V>(smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R, V>, threads, smem) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st) {
@@ -401,27 +420,21 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaS
 
 // Resident CTAs per SM for a pass configuration (for grid sizing).
 int pass_occupancy(int precision, int V, int L) {
-    size_t smem = (precision == TUSQ_C128 ? 16 : 8) << L;
-    const int threads = 1 << (L - V);
-    int nb = 0;
-    cudaError_t e;
     if (precision == TUSQ_C128) {
         switch (V) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 1>, threads, smem); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 2>, threads, smem); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 3>, threads, smem); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<double, 4>, threads, smem); break;
-        }
-    } else {
-        switch (V) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 1>, threads, smem); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 2>, threads, smem); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 3>, threads, smem); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 4>, threads, smem); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<float, 5>, threads, smem); break;
+        case 1: return occupancy_t<double, 1>(L);
+        case 2: return occupancy_t<double, 2>(L);
+        case 3: return occupancy_t<double, 3>(L);
+        default: return occupancy_t<double, 4>(L);
         }
     }
-    return (e == cudaSuccess && nb > 0) ? nb : 1;
+    switch (V) {
+    case 1: return occupancy_t<float, 1>(L);
+    case 2: return occupancy_t<float, 2>(L);
+    case 3: return occupancy_t<float, 3>(L);
+    case 4: return occupancy_t<float, 4>(L);
+    default: return occupancy_t<float, 5>(L);
+    }
 }
 
 cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st) {

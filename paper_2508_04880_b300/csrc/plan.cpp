@@ -417,6 +417,48 @@ int build_plan_from_instances(const tusq_circuit &circ, uint64_t n_inst, const u
     return TUSQ_OK;
 }
 
+// Contiguous chunk `rank` of `world` of a plan's DFS order, balanced by the
+// DFTT gate work of each leaf (the first leaf of a chunk pays its whole
+// path, later ones the part below their branch slot).
+int build_plan_shard(const tusq_plan_t &src, int rank, int world, tusq_plan_t &P) {
+    const uint64_t N = src.n_inst();
+    std::vector<double> cost(N);
+    for (uint64_t i = 0; i < N; ++i) cost[i] = 1.0 + (i ? (double)(src.G - src.lcp[i - 1]) : (double)src.G);
+    double total = 0;
+    for (double c : cost) total += c;
+    // chunk r = leaves whose cumulative cost midpoint falls in [r, r+1) * total / world
+    uint64_t a = N, b = N;
+    double acc = 0;
+    for (uint64_t i = 0; i < N; ++i) {
+        double mid = acc + 0.5 * cost[i];
+        int r = (int)std::min<double>(world - 1, std::floor(mid * world / total));
+        if (r == rank && a == N) a = i;
+        if (r > rank && b == N) { b = i; break; }
+        acc += cost[i];
+    }
+    if (a == N) b = N;
+    P.n = src.n;
+    P.G = src.G;
+    P.gates = src.gates;
+    P.shots = src.shots;
+    P.seed = src.seed;
+    P.opts = src.opts;
+    std::memset(&P.stats, 0, sizeof P.stats);
+    P.stats.shots = src.shots;
+    P.stats.n_gates = src.G;
+    std::vector<Key> keys;
+    for (uint64_t i = a; i < b; ++i) {
+        Key k;
+        for (uint64_t e = src.ev_off[i]; e < src.ev_off[i + 1]; ++e)
+            k.push_back(pack_event(src.ev_slot[e], src.ev_qubit[e], src.ev_pauli[e]));
+        keys.push_back(k);
+    }
+    std::vector<Kept> kept;
+    for (uint64_t i = a; i < b; ++i) kept.push_back(Kept{&keys[i - a], src.counts[i], src.weights[i]});
+    finish_tree(P, kept);
+    return TUSQ_OK;
+}
+
 namespace {
 
 // Kept instances in DFS order -> flat event lists, branch slots between

@@ -301,4 +301,6 @@ WORKLOADS = {
     "random_layers_6q": lambda: random_layers(6, 20, 0, 1e-3, 1e-2),
     "brickwork_20q": lambda: brickwork(20, 40, 0, 1e-3, 1e-2),
     "qaoa_28q": lambda: qaoa_3regular(28, 4, 0, 5e-4, 5e-3),
+    # same recipe at 26 qubits (512 MiB complex64 state): the profiling case
+    "qaoa_26q": lambda: qaoa_3regular(26, 4, 0, 5e-4, 5e-3),
 }

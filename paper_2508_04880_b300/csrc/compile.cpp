@@ -231,9 +231,40 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
 
 // ------------------------------------------------------------- encoding
 
-inline uint32_t swz(uint32_t e, bool c128) {
-    if (c128) return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
-    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
+inline uint32_t swz(uint32_t e, bool c128) { return tile_swizzle(e, c128); }
+
+// Structure of a matrix op: real entries, or [[c, -is], [-is, c]].
+uint32_t mat1_sub(const cd *m) {
+    bool real = true;
+    for (int k = 0; k < 4; ++k) real = real && m[k].imag() == 0.0;
+    if (real) return SUB_REAL;
+    if (m[0] == m[3] && m[0].imag() == 0.0 && m[1] == m[2] && m[1].real() == 0.0) return SUB_RXTYPE;
+    return SUB_GENERAL;
+}
+
+// A 4x4 that exchanges two basis states and fixes the others (CX in some
+// basis order): returns true with the two states.
+bool mat2_swap(const cd *m, int &s0, int &s1) {
+    int perm[4];
+    for (int r = 0; r < 4; ++r) {
+        perm[r] = -1;
+        for (int c = 0; c < 4; ++c) {
+            if (m[4 * r + c] == cd(1, 0)) {
+                if (perm[r] >= 0) return false;
+                perm[r] = c;
+            } else if (m[4 * r + c] != cd(0, 0)) {
+                return false;
+            }
+        }
+        if (perm[r] < 0) return false;
+    }
+    int moved[4], nm = 0;
+    for (int r = 0; r < 4; ++r)
+        if (perm[r] != r) moved[nm++] = r;
+    if (nm != 2 || perm[moved[0]] != moved[1] || perm[moved[1]] != moved[0]) return false;
+    s0 = moved[0];
+    s1 = moved[1];
+    return true;
 }
 
 uint64_t to_fixed(double turns, bool c128) {
@@ -292,9 +323,14 @@ struct Encoder {
                 if (local[q] < 0) pd.cw[ncw++] = (uint8_t)q;
             pd.n_cw = ncw;
             pd.ntiles = 1ULL << ncw;
-            const int T = 1 << (L - v);
-            for (int i = 0; i < (1 << v); ++i) {
-                uint32_t e = (uint32_t)i * T;
+            // load rows: complex64 threads move adjacent pairs (local bit 0 in
+            // the registers, 16-byte accesses), so row i starts at local index
+            // i << (L - v + 1); complex128 threads move single amplitudes,
+            // row i at i << (L - v)
+            const int rsh = c128 ? L - v : L - v + 1;
+            const int nrow = c128 ? (1 << v) : (1 << (v - 1));
+            for (int i = 0; i < nrow; ++i) {
+                uint32_t e = (uint32_t)i << rsh;
                 uint64_t g = 0;
                 for (int b = 0; b < L; ++b)
                     if (e >> b & 1) g |= 1ULL << win[b];
@@ -333,9 +369,13 @@ struct Encoder {
                     if (o.type == H_MAT1) {
                         d.type = OP_MAT1;
                         d.a = regidx[local[o.q0]];
+                        d.sub = mat1_sub(o.m);
                         d.mat = (uint32_t)(prog.mats.size() / 32);
-                        for (int k = 0; k < 4; ++k) { prog.mats.push_back(o.m[k].real()); prog.mats.push_back(o.m[k].imag()); }
-                        for (int k = 4; k < 16; ++k) { prog.mats.push_back(0); prog.mats.push_back(0); }
+                        for (int k = 0; k < 16; ++k) {
+                            cd z = k < 4 ? o.m[k] : cd(0, 0);
+                            prog.mats.push_back(z.real());
+                            prog.mats.push_back(z.imag());
+                        }
                     } else if (o.type == H_MAT2) {
                         int ra = regidx[local[o.q0]], rb = regidx[local[o.q1]];
                         // device basis: k = bit_lo + 2 bit_hi over register bits lo < hi;
@@ -350,12 +390,14 @@ struct Encoder {
                             int b0 = (ra == lo) ? blo : bhi, b1 = (rb == lo) ? blo : bhi;
                             return 2 * b0 + b1;
                         };
+                        cd dm[16];
                         for (int r = 0; r < 4; ++r)
                             for (int c = 0; c < 4; ++c) {
-                                cd z = o.m[4 * l_of(r) + l_of(c)];
-                                prog.mats.push_back(z.real());
-                                prog.mats.push_back(z.imag());
+                                dm[4 * r + c] = o.m[4 * l_of(r) + l_of(c)];
+                                prog.mats.push_back(dm[4 * r + c].real());
+                                prog.mats.push_back(dm[4 * r + c].imag());
                             }
+                        d.sub = mat2_swap(dm, d.sw0, d.sw1) ? SUB_SWAP : SUB_GENERAL;
                     } else {
                         d.type = OP_DIAG;
                         d.phi0 = to_fixed(o.phi0, c128);
@@ -613,6 +655,7 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
     prog.n_snapshots = co.snapshots;
     Compiler c(P, co, prog);
     c.run();
+    prog.matsf.assign(prog.mats.begin(), prog.mats.end());
 }
 
 }  // namespace tusq

@@ -4,13 +4,17 @@
 // amplitudes that share every index bit outside a window of L qubits
 // (the window always contains the lowest qubits, so each tile is a set of
 // contiguous 128-byte runs).  A CTA loads a tile into shared memory with
-// coalesced loads, runs its register stages -- each thread gathers 2^V
-// amplitudes that differ in the stage's V register bits, applies the
-// stage's gates in registers (2x2, 4x4, diagonal phase runs), scatters
-// them back -- and writes the tile back, optionally also to a snapshot,
-// adding w|psi|^2 into the FP64 output (leaf) and producing partial sums
-// of the norm and a checksum (drift check).  Shared-memory addresses are
-// XOR-swizzled so that the gathers of every stage layout spread over banks.
+// coalesced 16-byte loads, runs its register stages -- each thread gathers
+// 2^V amplitudes that differ in the stage's V register bits, applies the
+// stage's gates in registers (2x2, 4x4, diagonal phase runs), scatters them
+// back -- and writes the tile back, optionally also to a snapshot, adding
+// w|psi|^2 into the FP64 output (leaf) and producing partial sums of the
+// norm and a checksum (drift check).  Shared-memory addresses are
+// XOR-swizzled (tile_swizzle) so that every stage layout spreads over banks.
+//
+// B300 has little FP64 throughput, so complex64 passes keep FP64 out of the
+// per-amplitude work: matrices come from an FP32 pool, partial sums are
+// FP32 within a tile, and the leaf update costs one FP64 add per amplitude.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,36 +32,67 @@ template <typename C2> __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
     r.y = a.x * b.y + a.y * b.x;
     return r;
 }
+// a * b + c
 template <typename C2> __device__ __forceinline__ C2 cmad(C2 a, C2 b, C2 c) {
-    // a * b + c
     C2 r;
     r.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
     r.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
     return r;
 }
 
-template <typename R> __device__ __forceinline__ typename C2T<R>::type load_mat(const double *m, int k);
-template <> __device__ __forceinline__ float2 load_mat<float>(const double *m, int k) {
-    return make_float2((float)__ldg(m + 2 * k), (float)__ldg(m + 2 * k + 1));
+// Matrix entry k of a slot: FP32 pool for complex64, FP64 pool for complex128.
+template <typename R> __device__ __forceinline__ typename C2T<R>::type mat_at(const PassArgs &A, uint32_t slot, int k);
+template <> __device__ __forceinline__ float2 mat_at<float>(const PassArgs &A, uint32_t slot, int k) {
+    return __ldg(reinterpret_cast<const float2 *>(A.matsf) + 16 * (size_t)slot + k);
 }
-template <> __device__ __forceinline__ double2 load_mat<double>(const double *m, int k) {
-    return make_double2(__ldg(m + 2 * k), __ldg(m + 2 * k + 1));
+template <> __device__ __forceinline__ double2 mat_at<double>(const PassArgs &A, uint32_t slot, int k) {
+    return __ldg(reinterpret_cast<const double2 *>(A.mats) + 16 * (size_t)slot + k);
 }
 
-// 2x2 on register bit B.
-template <int V, int B, typename C2>
+// 2x2 on register bit B; SUB picks the form (general, real, RX-type).
+template <int V, int B, int SUB, typename C2>
 __device__ __forceinline__ void apply1(C2 (&a)[1 << V], C2 m0, C2 m1, C2 m2, C2 m3) {
 #pragma unroll
     for (int r = 0; r < (1 << V); ++r) {
         if (r & (1 << B)) continue;
-        C2 x = a[r], y = a[r | (1 << B)];
-        C2 zero;
-        zero.x = 0;
-        zero.y = 0;
-        a[r] = cmad(m0, x, cmul(m1, y));
-        a[r | (1 << B)] = cmad(m2, x, cmul(m3, y));
-        (void)zero;
+        C2 x = a[r], y = a[r | (1 << B)], u, w;
+        if constexpr (SUB == SUB_REAL) {
+            u.x = fma(m0.x, x.x, m1.x * y.x);
+            u.y = fma(m0.x, x.y, m1.x * y.y);
+            w.x = fma(m2.x, x.x, m3.x * y.x);
+            w.y = fma(m2.x, x.y, m3.x * y.y);
+        } else if constexpr (SUB == SUB_RXTYPE) {
+            // [[c, -is], [-is, c]] with c = m0.x, -s = m1.y
+            u.x = fma(m0.x, x.x, -m1.y * y.y);
+            u.y = fma(m0.x, x.y, m1.y * y.x);
+            w.x = fma(m0.x, y.x, -m1.y * x.y);
+            w.y = fma(m0.x, y.y, m1.y * x.x);
+        } else {
+            u = cmad(m0, x, cmul(m1, y));
+            w = cmad(m2, x, cmul(m3, y));
+        }
+        a[r] = u;
+        a[r | (1 << B)] = w;
     }
+}
+
+template <int V, int SUB, typename C2>
+__device__ __forceinline__ void dispatch1b(C2 (&a)[1 << V], int b, C2 m0, C2 m1, C2 m2, C2 m3) {
+    switch (b) {
+    case 0: apply1<V, 0, SUB>(a, m0, m1, m2, m3); break;
+    case 1: if constexpr (V > 1) apply1<V, 1, SUB>(a, m0, m1, m2, m3); break;
+    case 2: if constexpr (V > 2) apply1<V, 2, SUB>(a, m0, m1, m2, m3); break;
+    case 3: if constexpr (V > 3) apply1<V, 3, SUB>(a, m0, m1, m2, m3); break;
+    case 4: if constexpr (V > 4) apply1<V, 4, SUB>(a, m0, m1, m2, m3); break;
+    default: break;
+    }
+}
+
+template <int V, typename C2>
+__device__ __forceinline__ void dispatch1(C2 (&a)[1 << V], int b, uint32_t sub, C2 m0, C2 m1, C2 m2, C2 m3) {
+    if (sub == SUB_REAL) dispatch1b<V, SUB_REAL>(a, b, m0, m1, m2, m3);
+    else if (sub == SUB_RXTYPE) dispatch1b<V, SUB_RXTYPE>(a, b, m0, m1, m2, m3);
+    else dispatch1b<V, SUB_GENERAL>(a, b, m0, m1, m2, m3);
 }
 
 // 4x4 on register bits A < B, basis k = bit_A + 2 bit_B.
@@ -75,20 +110,50 @@ __device__ __forceinline__ void apply2(C2 (&a)[1 << V], const C2 (&m)[16]) {
     }
 }
 
-template <int V, typename C2>
-__device__ __forceinline__ void dispatch1(C2 (&a)[1 << V], int b, C2 m0, C2 m1, C2 m2, C2 m3) {
-    switch (b) {
-    case 0: apply1<V, 0>(a, m0, m1, m2, m3); break;
-    case 1: if constexpr (V > 1) apply1<V, 1>(a, m0, m1, m2, m3); break;
-    case 2: if constexpr (V > 2) apply1<V, 2>(a, m0, m1, m2, m3); break;
-    case 3: if constexpr (V > 3) apply1<V, 3>(a, m0, m1, m2, m3); break;
-    case 4: if constexpr (V > 4) apply1<V, 4>(a, m0, m1, m2, m3); break;
-    default: break;
+// Exchange of basis states s0, s1 of every quad on register bits A < B.
+template <int V, int A, int B, typename C2>
+__device__ __forceinline__ void swap2(C2 (&a)[1 << V], int s0, int s1) {
+#pragma unroll
+    for (int r = 0; r < (1 << V); ++r) {
+        if (r & ((1 << A) | (1 << B))) continue;
+        const int idx[4] = {r, r | (1 << A), r | (1 << B), r | (1 << A) | (1 << B)};
+        C2 v[4] = {a[idx[0]], a[idx[1]], a[idx[2]], a[idx[3]]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            C2 o = v[q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (p == q) continue;
+                const bool take = (q == s0 && p == s1) || (q == s1 && p == s0);
+                o.x = take ? v[p].x : o.x;
+                o.y = take ? v[p].y : o.y;
+            }
+            a[idx[q]] = o;
+        }
     }
 }
 
 template <int V, typename C2>
-__device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], int lo, int hi, const C2 (&m)[16]) {
+__device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], const DevOp &op, const PassArgs &A) {
+    using R = decltype(C2{}.x);
+    const int lo = op.a, hi = op.b;
+    if (op.sub == SUB_SWAP) {
+        const int s0 = op.sw0, s1 = op.sw1;
+#define TUSQ_CASES(X, Y) \
+    case X * 8 + Y: if constexpr (V > Y) swap2<V, X, Y>(a, s0, s1); break;
+        switch (lo * 8 + hi) {
+            TUSQ_CASES(0, 1) TUSQ_CASES(0, 2) TUSQ_CASES(0, 3) TUSQ_CASES(0, 4)
+            TUSQ_CASES(1, 2) TUSQ_CASES(1, 3) TUSQ_CASES(1, 4)
+            TUSQ_CASES(2, 3) TUSQ_CASES(2, 4)
+            TUSQ_CASES(3, 4)
+        default: break;
+        }
+#undef TUSQ_CASES
+        return;
+    }
+    C2 m[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) m[q] = mat_at<R>(A, op.mat, q);
 #define TUSQ_CASE2(X, Y) \
     case X * 8 + Y: if constexpr (V > Y) apply2<V, X, Y>(a, m); break;
     switch (lo * 8 + hi) {
@@ -105,12 +170,15 @@ __device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], int lo, int hi, const
 template <typename R> struct Phase;
 template <> struct Phase<float> {
     using U = uint32_t;
-    static constexpr U kMask = 0x7FFFFFFFu;
+    // 2^-31-turn units; the low 31 bits, read as a signed 32-bit fraction of a
+    // turn, give the exact angle reduced to [-pi, pi) before the fast
+    // hardware sine and cosine (absolute error about 4e-7 there).
     __device__ static float2 unit(U p) {
-        float t = (float)(p & kMask) * 4.656612873077393e-10f;   // 2^-31 turns
-        float s, c;
-        sincospif(2.0f * t, &s, &c);
-        return make_float2(c, s);
+        const int32_t s = (int32_t)(p << 1);
+        const float x = (float)s * 1.4629180792671596e-09f;   // 2 pi / 2^32
+        float sn, cs;
+        __sincosf(x, &sn, &cs);
+        return make_float2(cs, sn);
     }
 };
 template <> struct Phase<double> {
@@ -173,11 +241,6 @@ __device__ __forceinline__ void apply_diag(typename C2T<R>::type (&a)[1 << V], c
     }
 }
 
-__device__ __forceinline__ uint32_t swz(uint32_t e, bool c128) {
-    if (c128) return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
-    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
-}
-
 // Sign +-1 of the checksum weight of global index x (a 32-bit integer hash
 // of x folded to 32 bits; C. Wellons' "lowbias32" mixer).
 __device__ __forceinline__ float check_sign(uint64_t x) {
@@ -190,12 +253,27 @@ __device__ __forceinline__ float check_sign(uint64_t x) {
     return (h >> 31) ? -1.0f : 1.0f;
 }
 
+// FP32 -> FP64 by bit manipulation on the integer pipes (the conversion
+// instruction runs on B300's scarce FP64 units).  Exact for normal
+// non-negative inputs; zero and subnormal inputs give 0.
+__device__ __forceinline__ double f32_to_f64_nonneg(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const uint64_t bits = ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// Leaf update of one output element: acc += w p (p, w in FP32 for complex64).
+__device__ __forceinline__ double leaf_add(double acc, float wp) { return acc + f32_to_f64_nonneg(wp); }
 
 template <typename R, int V>
-__global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassArgs args) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
+    // complex64 threads move adjacent pairs in the load/store phases
+    constexpr int NROW = kC128 ? NR : NR / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *tile = reinterpret_cast<C2 *>(smem_raw);
     const PassDesc &d = args.d;
@@ -205,11 +283,13 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassA
     C2 *snap = reinterpret_cast<C2 *>(args.snap);
     const uint32_t flags = d.flags;
 
-    // this thread's part of a load row: local index tid -> global offset
+    // this thread's part of a load row (local index tid, or 2 tid for pairs)
+    const uint32_t erow = kC128 ? (uint32_t)tid : (uint32_t)tid << 1;
     uint64_t gthr = 0;
-    for (int b = 0; b < L - V; ++b)
-        if (tid >> b & 1) gthr |= 1ull << d.win[b];
-    const uint32_t sthr = swz((uint32_t)tid, kC128);
+    for (int b = 0; b < L; ++b)
+        if (erow >> b & 1) gthr |= 1ull << d.win[b];
+    const uint32_t sthr = tile_swizzle(erow, kC128);
+    const float wleaf = (float)d.leaf_w;
 
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
 
@@ -218,9 +298,16 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassA
         for (int b = 0; b < d.n_cw; ++b)
             if (t >> b & 1) tb |= 1ull << d.cw[b];
         const uint64_t gbase = tb | gthr;
-        // load the tile
+        // load the tile (16-byte accesses)
+        if constexpr (kC128) {
 #pragma unroll
-        for (int i = 0; i < NR; ++i) tile[sthr ^ d.srow[i]] = state[gbase | d.grow[i]];
+            for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = state[gbase | d.grow[i]];
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(state);
+            float4 *dst = reinterpret_cast<float4 *>(tile);
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = src[(gbase | d.grow[i]) >> 1];
+        }
         __syncthreads();
         for (int s = 0; s < d.n_stages; ++s) {
             const StageDesc &sd = d.st[s];
@@ -233,7 +320,7 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassA
                     e |= 1u << sd.cpos[b];
                     gfix |= 1ull << d.win[sd.cpos[b]];
                 }
-            const uint32_t sb = swz(e, kC128);
+            const uint32_t sb = tile_swizzle(e, kC128);
             C2 a[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) a[r] = tile[sb ^ sd.sr[r]];
@@ -241,15 +328,10 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassA
                 const DevOp &op = args.ops[sd.op_begin + k];
                 const int type = op.type;
                 if (type == OP_MAT1) {
-                    const double *m = args.mats + 32 * (size_t)op.mat;
-                    dispatch1<V>(a, op.a, load_mat<R>(m, 0), load_mat<R>(m, 1), load_mat<R>(m, 2),
-                                 load_mat<R>(m, 3));
+                    dispatch1<V>(a, op.a, op.sub, mat_at<R>(args, op.mat, 0), mat_at<R>(args, op.mat, 1),
+                                 mat_at<R>(args, op.mat, 2), mat_at<R>(args, op.mat, 3));
                 } else if (type == OP_MAT2) {
-                    const double *m = args.mats + 32 * (size_t)op.mat;
-                    C2 mm[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) mm[q] = load_mat<R>(m, q);
-                    dispatch2<V>(a, op.a, op.b, mm);
+                    dispatch2<V>(a, op, args);
                 } else {
                     apply_diag<R, V>(a, op, args.tmask, args.tphi, gfix);
                 }
@@ -262,35 +344,48 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassA
         float pn = 0.f, pr = 0.f, pi = 0.f;
         double dn = 0.0, dr = 0.0, di = 0.0;
 #pragma unroll
-        for (int i = 0; i < NR; ++i) {
+        for (int i = 0; i < NROW; ++i) {
             const uint64_t g = gbase | d.grow[i];
-            C2 v = tile[sthr ^ d.srow[i]];
-            if (flags & PF_WRITE) state[g] = v;
-            if (flags & PF_SNAPSHOT) snap[g] = v;
-            if (flags & PF_LEAF) {
-                double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                args.acc[g] = fma(d.leaf_w, p, args.acc[g]);
-            }
-            if (flags & PF_REDUCE) {
-                float h = check_sign(g);
-                if constexpr (kC128) {
+            if constexpr (kC128) {
+                C2 v = tile[sthr ^ d.srow[i]];
+                if (flags & PF_WRITE) state[g] = v;
+                if (flags & PF_SNAPSHOT) snap[g] = v;
+                if (flags & PF_LEAF) args.acc[g] = fma(d.leaf_w, v.x * v.x + v.y * v.y, args.acc[g]);
+                if (flags & PF_REDUCE) {
+                    const double h = check_sign(g);
                     dn += v.x * v.x + v.y * v.y;
                     dr += h * v.x;
                     di += h * v.y;
-                } else {
+                }
+            } else {
+                const float4 v = reinterpret_cast<const float4 *>(tile)[(sthr ^ d.srow[i]) >> 1];
+                if (flags & PF_WRITE) reinterpret_cast<float4 *>(state)[g >> 1] = v;
+                if (flags & PF_SNAPSHOT) reinterpret_cast<float4 *>(snap)[g >> 1] = v;
+                if (flags & PF_LEAF) {
+                    double2 *ap = reinterpret_cast<double2 *>(args.acc) + (g >> 1);
+                    double2 acc = *ap;
+                    acc.x = leaf_add(acc.x, wleaf * fmaf(v.x, v.x, v.y * v.y));
+                    acc.y = leaf_add(acc.y, wleaf * fmaf(v.z, v.z, v.w * v.w));
+                    *ap = acc;
+                }
+                if (flags & PF_REDUCE) {
+                    const float h0 = check_sign(g), h1 = check_sign(g | 1);
                     pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
-                    pr = fmaf(h, v.x, pr);
-                    pi = fmaf(h, v.y, pi);
+                    pn = fmaf(v.z, v.z, fmaf(v.w, v.w, pn));
+                    pr = fmaf(h0, v.x, fmaf(h1, v.z, pr));
+                    pi = fmaf(h0, v.y, fmaf(h1, v.w, pi));
                 }
             }
         }
-        red_n += (double)pn + dn;
-        red_r += (double)pr + dr;
-        red_i += (double)pi + di;
+        if (flags & PF_REDUCE) {
+            red_n += (double)pn + dn;
+            red_r += (double)pr + dr;
+            red_i += (double)pi + di;
+        }
         __syncthreads();
     }
     if (flags & PF_REDUCE) {
-        // fixed-order block reduction: warp shuffles, then warp 0
+        // fixed-order block reduction: warp shuffles, then thread 0
         __shared__ double wsum[3][32];
         for (int off = 16; off > 0; off >>= 1) {
             red_n += __shfl_down_sync(0xffffffffu, red_n, off);

@@ -16,6 +16,26 @@ constexpr int kRegBitsC128 = 4;      // 2^4 (complex128)
 
 enum DevOpType : int32_t { OP_MAT1 = 1, OP_MAT2 = 2, OP_DIAG = 3 };
 
+// Structure of a matrix op (DevOp::sub), chosen on the host so the kernel
+// spends fewer FMAs: MAT1 general / real entries / [[c, -is], [-is, c]];
+// MAT2 general / a swap of two basis states (CX in some basis order).
+enum DevOpSub : uint32_t { SUB_GENERAL = 0, SUB_REAL = 1, SUB_RXTYPE = 2, SUB_SWAP = 3 };
+
+#if defined(__CUDACC__)
+#define TUSQ_HD __host__ __device__ __forceinline__
+#else
+#define TUSQ_HD inline
+#endif
+
+// Shared-memory swizzle of a tile's local index (XOR-linear bijection).
+// complex64 (8-byte elements): bits 1..3 take the xor of the higher bits in
+// groups of three, bit 0 stays, so a pair (2e, 2e+1) stays adjacent for
+// 16-byte accesses.  complex128 (16-byte elements): bits 0..2.
+TUSQ_HD uint32_t tile_swizzle(uint32_t e, bool c128) {
+    if (c128) return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7u);
+    return e ^ ((((e >> 4) ^ (e >> 7) ^ (e >> 10)) & 7u) << 1);
+}
+
 // One operation of a stage, on the register bits of that stage.
 //   MAT1: 2x2 on register bit a (row-major, basis bit a).
 //   MAT2: 4x4 on register bits a < b, basis index bit_a + 2*bit_b.
@@ -28,10 +48,11 @@ struct DevOp {
     int32_t a, b;
     uint32_t mat;          // index of the 4x4 slot in the matrix pools
     uint32_t term_begin;   // DIAG: first term
-    uint32_t pad0;
+    uint32_t sub;          // DevOpSub
     uint64_t phi0;         // DIAG: constant phase (fixed point)
     uint16_t csr[34];      // DIAG: term offsets per register mask mu (relative)
-    uint32_t pad1[3];
+    int32_t sw0, sw1;      // SUB_SWAP: the two basis states exchanged (0..3)
+    uint32_t pad1;
 };
 static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
 
@@ -91,6 +112,7 @@ struct Program {
     std::vector<PassDesc> passes;
     std::vector<DevOp> ops;
     std::vector<double> mats;        // 32 doubles (16 complex) per matrix slot
+    std::vector<float> matsf;        // the same slots in FP32 (complex64 kernels)
     std::vector<uint64_t> term_mask;
     std::vector<uint64_t> term_phi;
     int max_depth = 0;
@@ -110,6 +132,7 @@ struct PassArgs {
     double *partials;     // 3 doubles per CTA for PF_REDUCE
     const DevOp *ops;
     const double *mats;
+    const float *matsf;
     const uint64_t *tmask;
     const uint64_t *tphi;
 };

@@ -49,6 +49,7 @@ struct tusq_exec {
     unsigned long long *counters = nullptr;
     DevOp *ops = nullptr;
     double *mats = nullptr;
+    float *matsf = nullptr;
     uint64_t *tmask = nullptr, *tphi = nullptr;
     std::vector<int> grid_of_pass;
     int max_grid = 1;
@@ -86,7 +87,7 @@ int dmalloc(T **p, size_t bytes, cudaStream_t st) {
 
 void release(tusq_exec *e) {
     void *bufs[] = {e->state, e->snaps, e->records, e->partials, e->drift_log, e->restore_flag,
-                    e->counters, e->ops, e->mats, e->tmask, e->tphi};
+                    e->counters, e->ops, e->mats, e->matsf, e->tmask, e->tphi};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, e->stream);
     e->state = e->snaps = nullptr;
@@ -95,6 +96,7 @@ void release(tusq_exec *e) {
     e->counters = nullptr;
     e->ops = nullptr;
     e->mats = nullptr;
+    e->matsf = nullptr;
     e->tmask = e->tphi = nullptr;
 }
 
@@ -156,6 +158,7 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
     info->kernel_launches = launches;
     info->algorithmic_bytes = bytes;
     info->program_bytes = (double)(sizeof(DevOp) * pg.ops.size() + sizeof(double) * pg.mats.size() +
+                                   sizeof(float) * pg.matsf.size() +
                                    sizeof(uint64_t) * (pg.term_mask.size() + pg.term_phi.size()));
 }
 
@@ -228,6 +231,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     ALLOC(e->counters, sizeof(unsigned long long) * 4);
     ALLOC(e->ops, sizeof(DevOp) * std::max<size_t>(pg.ops.size(), 1));
     ALLOC(e->mats, sizeof(double) * std::max<size_t>(pg.mats.size(), 1));
+    ALLOC(e->matsf, sizeof(float) * std::max<size_t>(pg.matsf.size(), 1));
     ALLOC(e->tmask, sizeof(uint64_t) * std::max<size_t>(pg.term_mask.size(), 1));
     ALLOC(e->tphi, sizeof(uint64_t) * std::max<size_t>(pg.term_phi.size(), 1));
 #undef ALLOC
@@ -239,6 +243,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     };
     if ((rc = up(e->ops, pg.ops.data(), sizeof(DevOp) * pg.ops.size())) ||
         (rc = up(e->mats, pg.mats.data(), sizeof(double) * pg.mats.size())) ||
+        (rc = up(e->matsf, pg.matsf.data(), sizeof(float) * pg.matsf.size())) ||
         (rc = up(e->tmask, pg.term_mask.data(), sizeof(uint64_t) * pg.term_mask.size())) ||
         (rc = up(e->tphi, pg.term_phi.data(), sizeof(uint64_t) * pg.term_phi.size()))) {
         release(e);
@@ -297,6 +302,7 @@ int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
             a.partials = e->partials;
             a.ops = e->ops;
             a.mats = e->mats;
+            a.matsf = e->matsf;
             a.tmask = e->tmask;
             a.tphi = e->tphi;
             last_grid = e->grid_of_pass[s.pass];
@@ -401,8 +407,8 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
         set_error(std::string(who) + ": bad traversal");
         return TUSQ_EINVAL;
     }
-    if (o.max_window < 0 || o.max_window > kMaxTileBits) {
-        set_error(std::string(who) + ": max_window must be in [0, 14]");
+    if (o.max_window != 0 && (o.max_window < 4 || o.max_window > kMaxTileBits)) {
+        set_error(std::string(who) + ": max_window must be 0 (default) or in [4, 14]");
         return TUSQ_EINVAL;
     }
     if (o.snapshot_bytes == 0) o.snapshot_bytes = (uint64_t)8 * ((uint64_t)(o.precision == TUSQ_C128 ? 16 : 8) << p->n);

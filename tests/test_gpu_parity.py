@@ -1,9 +1,10 @@
 """GPU parity: the CUDA DFTT engine (through the C ABI) against the CPU
 oracle, element by element, on the same seeded inputs.
 
-Tolerances: complex128 mode 1e-12 max-abs and total variation; complex64
-mode max-abs 1e-5 and total variation 1e-4 (the stated bar for FP32
-state with FP64 leaf accumulation)."""
+Tolerances: complex128 mode max-abs 1e-12 per outcome (total variation
+1e-10: thousands of uncompute passes leave ~1e-14 per outcome, summed over
+up to 2^11 outcomes here); complex64 mode max-abs 1e-5 and total variation
+1e-4 (FP32 state with FP64 leaf accumulation)."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ import tusq_workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {T.C128: (1e-12, 1e-12), T.C64: (1e-5, 1e-4)}
+TOL = {T.C128: (1e-12, 1e-10), T.C64: (1e-5, 1e-4)}
 TRAVERSALS = [T.DFTT, T.FROM_SCRATCH, T.DFTT_SNAPSHOT]
 
 
@@ -155,12 +156,3 @@ def test_c64_vs_c128_brickwork():
     got, _ = gpu_run(sub, precision=T.C128)
     assert_close(got, ref, T.C128)
 
-
-def test_plan_from_instances_validation():
-    circ = T.circuit_from(W.ghz(3, 0.1, 0.1))
-    with pytest.raises(T.TusqError):
-        T.tusq_plan_from_instances(circ, [((0, 5, 1),)], [1.0])        # qubit out of range
-    with pytest.raises(T.TusqError):
-        T.tusq_plan_from_instances(circ, [((1, 0, 1), (0, 1, 1))], [1.0])   # unsorted
-    with pytest.raises(T.TusqError):
-        T.tusq_plan_from_instances(circ, [(), ()], [0.5, 0.5])            # duplicates

@@ -108,6 +108,22 @@ def test_plan_rejects_bad_input():
         T.tusq_plan(c, 0, 0)
 
 
+def test_plan_from_instances():
+    circ = T.circuit_from(W.ghz(3, 0.1, 0.1))
+    with pytest.raises(T.TusqError):
+        T.tusq_plan_from_instances(circ, [((0, 5, 1),)], [1.0])            # qubit out of range
+    with pytest.raises(T.TusqError):
+        T.tusq_plan_from_instances(circ, [((1, 0, 1), (0, 1, 1))], [1.0])  # unsorted
+    with pytest.raises(T.TusqError):
+        T.tusq_plan_from_instances(circ, [(), ()], [0.5, 0.5])             # duplicates
+    # a valid list comes back in DFS order with its branch slots
+    pl = T.tusq_plan_from_instances(circ, [(), ((1, 0, 3),), ((0, 2, 1), (2, 1, 2))], [0.5, 0.3, 0.2])
+    inst, counts, w, lcp = pl.instances()
+    assert inst == [((0, 2, 1), (2, 1, 2)), ((1, 0, 3),), ()]
+    assert list(w) == [0.2, 0.3, 0.5]
+    assert list(lcp) == [0, 1]
+
+
 def _header_symbols():
     src = open(os.path.join(ROOT, "include", "tusq.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)

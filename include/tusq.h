@@ -265,6 +265,38 @@ void tusq_exec_free(tusq_exec *e);
 int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
              void *cuda_stream);
 
+/* ------------------------------------------------- allocation-free run */
+
+/* Size of the static device scratch used by tusq_run_noalloc (32 MiB). */
+#define TUSQ_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* One traversal of `p` exactly as tusq_run computes it, but without
+ * allocating any device memory: for callers that cannot call cudaMalloc --
+ * e.g. an application whose device memory is owned entirely by its own pool
+ * allocator, or a plugin host that only lends out buffers it allocated
+ * itself.  (The paper has no counterpart; this is a deployment option.)
+ *
+ * All scratch -- the state, the device program, the drift-check records and
+ * reduction partials, and as many branch snapshots as fit -- lives in one
+ * static __device__ array of TUSQ_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit.  The caller passes the plan and
+ * probs_dev (caller-owned device buffer of 2^n doubles, zeroed here and
+ * filled with sum_i w_i |psi_i|^2) and a stream (cudaStream_t, NULL = legacy
+ * default stream).  No cudaMalloc, cudaFree or allocating library routine is
+ * called; host memory is used for compiling the program.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and keeps
+ * the last call's contents (what must start at zero is cleared on entry):
+ * calls whose work overlaps on the GPU race with each other.  The call
+ * synchronises `cuda_stream` before returning and fills *info if given.
+ * Errors: TUSQ_EINVAL with a message when the state (more than half the
+ * scratch) or state + program do not fit -- use tusq_run then; TUSQ_ECUDA,
+ * TUSQ_EDRIFT as tusq_run. */
+int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
+                     void *cuda_stream, tusq_run_info_t *info);
+
 /* -------------------------------------------------------------- serving */
 
 /* A serving loop that admits jobs while their device footprint

@@ -36,7 +36,7 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_free",
-    "tusq_run", "tusq_server_create", "tusq_submit", "tusq_poll", "tusq_server_drain",
+    "tusq_run", "tusq_run_noalloc", "tusq_server_create", "tusq_submit", "tusq_poll", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
 
@@ -114,6 +114,7 @@ def _load():
         "tusq_exec_pass_profile": (i32, [vp, P(u64), P(P(ctypes.c_float)), P(P(f64))]),
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
+        "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
         "tusq_server_create": (i32, [ctypes.c_size_t, i32, P(vp)]),
         "tusq_submit": (i32, [vp, vp, P(RunOpts), vp, P(u64)]),
         "tusq_poll": (i32, [vp, u64, P(i32), P(f64)]),
@@ -350,6 +351,16 @@ def tusq_compile_stats(plan: Plan, opts: Optional[RunOpts] = None) -> dict:
 def tusq_run(plan: Plan, probs_ptr: int, opts: Optional[RunOpts] = None, stream: int = 0) -> None:
     o = opts or run_opts()
     _check(lib.tusq_run(plan.h, ctypes.byref(o), ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream)))
+
+
+def tusq_run_noalloc(plan: Plan, probs_ptr: int, opts: Optional[RunOpts] = None, stream: int = 0) -> dict:
+    """One traversal with every scratch buffer in the library's static
+    device array (no device allocation); returns the run counters."""
+    o = opts or run_opts()
+    info = RunInfo()
+    _check(lib.tusq_run_noalloc(plan.h, ctypes.byref(o), ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream),
+                                ctypes.byref(info)))
+    return info.as_dict()
 
 
 def run_torch(plan: Plan, opts: Optional[RunOpts] = None, device: str = "cuda"):

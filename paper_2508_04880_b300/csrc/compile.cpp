@@ -140,49 +140,92 @@ struct Pass {
 };
 
 // Greedy list scheduling over the dependence DAG of `ops` (two ops depend
-// on each other if they share a qubit, unless both are diagonal): a group
-// takes every ready op whose bits (qubits_of, for non-diagonal ops) fit its
-// window of `cap` bits, growing the window while there is room, in list
-// order; diagonal ops fit any window.
+// on each other if they share a qubit, unless both are diagonal).  A group
+// has a window of at most `cap` bits (qubits_of gives the bits of a
+// non-diagonal op; diagonal ops fit any window) and takes every op that
+// becomes ready and fits.  When nothing more fits, the window grows by the
+// bits of one blocked ready op: the choice that lets the most ops into the
+// group (found by trying each candidate on a copy of the DAG state).
 template <class QubitsOf>
 std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uint64_t forced,
                                        QubitsOf qubits_of, std::vector<uint64_t> *wins) {
     const int m = (int)ops.size();
-    std::vector<std::vector<int>> preds(m);
-    std::vector<uint64_t> qm(m);
-    for (int b = 0; b < m; ++b) qm[b] = ops[b].qmask();
+    std::vector<std::vector<int>> succ(m);
+    std::vector<int> indeg(m, 0);
+    std::vector<uint64_t> qm(m), wq(m);
     for (int b = 0; b < m; ++b) {
+        qm[b] = ops[b].qmask();
+        wq[b] = ops[b].type == H_DIAG ? 0 : qubits_of(ops[b]);
+    }
+    for (int b = 0; b < m; ++b)
         for (int a = 0; a < b; ++a) {
             if (ops[a].type == H_DIAG && ops[b].type == H_DIAG) continue;
-            if (qm[a] & qm[b]) preds[b].push_back(a);
+            if (qm[a] & qm[b]) {
+                succ[a].push_back(b);
+                indeg[b]++;
+            }
         }
-    }
     std::vector<char> done(m, 0);
+    std::vector<int> ready;       // ready and not yet scheduled (blocked by the window)
+    for (int b = 0; b < m; ++b)
+        if (indeg[b] == 0) ready.push_back(b);
+    // schedule everything that fits W, starting from `ready`; returns the
+    // scheduled ops in application order and leaves the blocked ones in ready
+    auto closure = [&](uint64_t W, std::vector<int> &deg, std::vector<char> &dn, std::vector<int> &rdy,
+                       std::vector<int> *out) {
+        int count = 0;
+        std::vector<int> work;
+        std::vector<int> blocked;
+        std::sort(rdy.begin(), rdy.end());
+        for (int b : rdy) work.push_back(b);
+        rdy.clear();
+        size_t h = 0;
+        while (h < work.size()) {
+            int b = work[h++];
+            if ((wq[b] & ~W) != 0) { blocked.push_back(b); continue; }
+            dn[b] = 1;
+            ++count;
+            if (out) out->push_back(b);
+            for (int s : succ[b])
+                if (--deg[s] == 0) work.push_back(s);
+        }
+        rdy = blocked;
+        return count;
+    };
     int left = m;
     std::vector<std::vector<int>> groups;
     while (left > 0) {
         uint64_t W = forced;
         std::vector<int> g;
-        bool progress = true;
-        while (progress) {
-            progress = false;
-            for (int b = 0; b < m; ++b) {
-                if (done[b]) continue;
-                bool ready = true;
-                for (int a : preds[b]) if (!done[a]) { ready = false; break; }
-                if (!ready) continue;
-                if (ops[b].type != H_DIAG) {
-                    uint64_t q = qubits_of(ops[b]);
-                    if ((q & ~W) != 0) {
-                        if (__builtin_popcountll(W | q) > cap) continue;
-                        W |= q;
-                    }
+        left -= closure(W, indeg, done, ready, &g);
+        for (;;) {
+            // candidate window extensions: the bits of each blocked ready op
+            int best = -1;
+            int best_gain = -1;
+            uint64_t best_q = 0;
+            std::vector<uint64_t> tried;
+            for (int b : ready) {
+                uint64_t q = wq[b] & ~W;
+                if (__builtin_popcountll(W | q) > cap) continue;
+                if (std::find(tried.begin(), tried.end(), q) != tried.end()) continue;
+                tried.push_back(q);
+                std::vector<int> deg2 = indeg;
+                std::vector<char> dn2 = done;
+                std::vector<int> rdy2 = ready;
+                int gain = closure(W | q, deg2, dn2, rdy2, nullptr);
+                int nb = __builtin_popcountll(q);
+                // most ops per added bit first, then fewer bits, then list order
+                if (best < 0 || gain > best_gain ||
+                    (gain == best_gain &&
+                     nb < __builtin_popcountll(best_q))) {
+                    best = b;
+                    best_gain = gain;
+                    best_q = q;
                 }
-                done[b] = 1;
-                --left;
-                g.push_back(b);
-                progress = true;
             }
+            if (best < 0) break;
+            W |= best_q;
+            left -= closure(W, indeg, done, ready, &g);
         }
         if (g.empty()) throw std::logic_error("schedule: no progress (gate wider than window?)");
         groups.push_back(g);

@@ -246,7 +246,8 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
     for (const HOp &o : in) {
         if (!out.empty()) {
             HOp &p = out.back();
-            if (o.type == H_DIAG && p.type == H_DIAG) {
+            if (o.type == H_DIAG && p.type == H_DIAG &&
+                p.terms.size() + o.terms.size() <= (size_t)kMaxDiagTerms) {
                 p.phi0 += o.phi0;
                 for (auto &t : o.terms) {
                     bool hit = false;
@@ -327,9 +328,10 @@ struct Encoder {
     int Lmax;
 
     // Encode one pass (window + ops already in application order) into
-    // PassDescs (several if the register stages exceed kMaxStages; only the
-    // last one carries `flags`).  last_uids receives the uids of the ops in
-    // that last PassDesc.
+    // PassDescs: several when the register stages exceed kMaxStages or the
+    // program (ops, matrix slots, diagonal terms) exceeds the shared-memory
+    // budget; only the last one carries `flags`.  last_uids receives the uids
+    // of the ops in that last PassDesc.
     void emit(const std::vector<int> &win, const std::vector<HOp> &ops_in, uint32_t flags,
               double leaf_w, int snap, std::vector<int> &pass_ids, std::vector<int> *last_uids) {
         if (last_uids) last_uids->clear();
@@ -347,19 +349,48 @@ struct Encoder {
         };
         const int v = std::min(V, L);
         std::vector<uint64_t> swin;
-        std::vector<std::vector<int>> stages;
-        if (!ops.empty()) stages = schedule(ops, v, 0, lq, &swin);
-        size_t s0 = 0;
+        std::vector<std::vector<int>> sched;
+        if (!ops.empty()) sched = schedule(ops, v, 0, lq, &swin);
+        // stage pieces of at most kMaxStageOps ops (a long stage is cut into
+        // several with the same register bits)
+        struct Piece { uint64_t R; std::vector<int> ops; };
+        std::vector<Piece> pieces;
+        for (size_t s = 0; s < sched.size(); ++s)
+            for (size_t k = 0; k < sched[s].size(); k += kMaxStageOps)
+                pieces.push_back(Piece{swin[s], std::vector<int>(sched[s].begin() + k,
+                    sched[s].begin() + std::min(sched[s].size(), k + (size_t)kMaxStageOps))});
+        const uint32_t mat_bytes = c128 ? 256 : 128;
+        auto piece_bytes = [&](const Piece &pc) {
+            uint32_t b = 0;
+            for (int oi : pc.ops) {
+                b += sizeof(DevOp);
+                if (ops[oi].type == H_DIAG) b += 16 * (uint32_t)ops[oi].terms.size();
+                else b += mat_bytes;
+            }
+            return b;
+        };
+        size_t p0 = 0;
         do {
-            size_t s1 = std::min(stages.size(), s0 + kMaxStages);
+            // as many pieces as the stage and program limits allow
+            size_t p1 = p0;
+            uint32_t bytes = 0;
+            while (p1 < pieces.size() && (int)(p1 - p0) < kMaxStages) {
+                uint32_t b = piece_bytes(pieces[p1]);
+                if (p1 > p0 && bytes + b > kMaxPassProgramBytes) break;
+                bytes += b;
+                ++p1;
+            }
             PassDesc pd;
             std::memset(&pd, 0, sizeof pd);
             pd.L = L;
-            pd.n_stages = (int)(s1 - s0);
-            bool last = (s1 >= stages.size());
+            pd.n_stages = (int)(p1 - p0);
+            bool last = (p1 >= pieces.size());
             pd.flags = last ? flags : PF_WRITE;
             pd.leaf_w = leaf_w;
             pd.snap = snap;
+            pd.op0 = (uint32_t)prog.ops.size();
+            pd.mat0 = (uint32_t)(prog.mats.size() / 32);
+            pd.term0 = (uint32_t)prog.term_mask.size();
             for (int i = 0; i < L; ++i) pd.win[i] = (uint8_t)win[i];
             int ncw = 0;
             for (int q = 0; q < n; ++q)
@@ -380,9 +411,9 @@ struct Encoder {
                 pd.grow[i] = g;
                 pd.srow[i] = (uint16_t)swz(e, c128);
             }
-            for (size_t s = s0; s < s1; ++s) {
-                StageDesc &sd = pd.st[s - s0];
-                uint64_t R = swin[s];
+            for (size_t s = p0; s < p1; ++s) {
+                StageDesc &sd = pd.st[s - p0];
+                uint64_t R = pieces[s].R;
                 // fill up to v register bits with the highest unused local bits
                 for (int b = L - 1; b >= 0 && __builtin_popcountll(R) < v; --b) R |= 1ULL << b;
                 int nr = 0, nc = 0;
@@ -390,7 +421,10 @@ struct Encoder {
                     if (R >> b & 1) sd.rbits[nr++] = (uint8_t)b;
                     else sd.cpos[nc++] = (uint8_t)b;
                 }
-                for (int i = 0; i < v; ++i) sd.greg[i] = 1ULL << win[sd.rbits[i]];
+                for (int i = 0; i < v; ++i) {
+                    sd.greg[i] = 1ULL << win[sd.rbits[i]];
+                    sd.sw1[i] = (uint16_t)swz(1u << sd.rbits[i], c128);
+                }
                 for (int r = 0; r < (1 << v); ++r) {
                     uint32_t e = 0;
                     for (int i = 0; i < v; ++i)
@@ -401,7 +435,7 @@ struct Encoder {
                 for (int i = 0; i < 64; ++i) regidx[i] = -1;
                 for (int i = 0; i < v; ++i) regidx[sd.rbits[i]] = i;
                 sd.op_begin = (uint32_t)prog.ops.size();
-                for (int oi : stages[s]) {
+                for (int oi : pieces[s].ops) {
                     const HOp &o = ops[oi];
                     if (last && last_uids) {
                         last_uids->push_back(o.uid);
@@ -469,10 +503,14 @@ struct Encoder {
                 }
                 sd.op_count = (uint32_t)(prog.ops.size() - sd.op_begin);
             }
+            pd.nops = (uint32_t)prog.ops.size() - pd.op0;
+            pd.nmat = (uint32_t)(prog.mats.size() / 32) - pd.mat0;
+            pd.nterm = (uint32_t)prog.term_mask.size() - pd.term0;
+            pd.prog_bytes = pd.nops * (uint32_t)sizeof(DevOp) + pd.nmat * mat_bytes + pd.nterm * 16;
             pass_ids.push_back((int)prog.passes.size());
             prog.passes.push_back(pd);
-            s0 = s1;
-        } while (s0 < stages.size());
+            p0 = p1;
+        } while (p0 < pieces.size());
     }
 };
 

@@ -40,14 +40,17 @@ template <typename C2> __device__ __forceinline__ C2 cmad(C2 a, C2 b, C2 c) {
     return r;
 }
 
-// Matrix entry k of a slot: FP32 pool for complex64, FP64 pool for complex128.
-template <typename R> __device__ __forceinline__ typename C2T<R>::type mat_at(const PassArgs &A, uint32_t slot, int k);
-template <> __device__ __forceinline__ float2 mat_at<float>(const PassArgs &A, uint32_t slot, int k) {
-    return __ldg(reinterpret_cast<const float2 *>(A.matsf) + 16 * (size_t)slot + k);
-}
-template <> __device__ __forceinline__ double2 mat_at<double>(const PassArgs &A, uint32_t slot, int k) {
-    return __ldg(reinterpret_cast<const double2 *>(A.mats) + 16 * (size_t)slot + k);
-}
+// A pass's program as copied into shared memory next to the tile: its ops,
+// matrix slots (16 complex entries each, FP32 for complex64) and diagonal
+// terms (mask, fixed-point phase), indexed relative to the pass's first one.
+template <typename R> struct SProg {
+    using C2 = typename C2T<R>::type;
+    const DevOp *ops;
+    const C2 *mats;
+    const uint64_t *terms;
+    uint32_t op0, mat0, term0;
+    __device__ __forceinline__ C2 mat(uint32_t slot, int k) const { return mats[16 * (slot - mat0) + k]; }
+};
 
 // 2x2 on register bit B; SUB picks the form (general, real, RX-type).
 template <int V, int B, int SUB, typename C2>
@@ -133,9 +136,9 @@ __device__ __forceinline__ void swap2(C2 (&a)[1 << V], int s0, int s1) {
     }
 }
 
-template <int V, typename C2>
-__device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], const DevOp &op, const PassArgs &A) {
-    using R = decltype(C2{}.x);
+template <int V, typename R>
+__device__ __forceinline__ void dispatch2(typename C2T<R>::type (&a)[1 << V], const DevOp &op, const SProg<R> &P) {
+    using C2 = typename C2T<R>::type;
     const int lo = op.a, hi = op.b;
     if (op.sub == SUB_SWAP) {
         const int s0 = op.sw0, s1 = op.sw1;
@@ -153,7 +156,7 @@ __device__ __forceinline__ void dispatch2(C2 (&a)[1 << V], const DevOp &op, cons
     }
     C2 m[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) m[q] = mat_at<R>(A, op.mat, q);
+    for (int q = 0; q < 16; ++q) m[q] = P.mat(op.mat, q);
 #define TUSQ_CASE2(X, Y) \
     case X * 8 + Y: if constexpr (V > Y) apply2<V, X, Y>(a, m); break;
     switch (lo * 8 + hi) {
@@ -199,24 +202,24 @@ template <> struct Phase<double> {
 // sum_mu C[mu] parity(r & mu) = (sum C - WHT(C)[r]) / 2).
 template <typename R, int V>
 __device__ __forceinline__ void apply_diag(typename C2T<R>::type (&a)[1 << V], const DevOp &op,
-                                           const uint64_t *__restrict__ tmask,
-                                           const uint64_t *__restrict__ tphi, uint64_t gfix) {
+                                           const SProg<R> &P, uint64_t gfix) {
     using U = typename Phase<R>::U;
     constexpr int NR = 1 << V;
     U A = (U)op.phi0;
     U C[NR];
 #pragma unroll
     for (int mu = 0; mu < NR; ++mu) C[mu] = 0;
-    const uint32_t tb = op.term_begin;
+    const ulonglong2 *tm = reinterpret_cast<const ulonglong2 *>(P.terms) + (op.term_begin - P.term0);
     for (int k = op.csr[0]; k < op.csr[1]; ++k) {
-        U ph = (U)__ldg(tphi + tb + k);
-        if (__popcll(gfix & __ldg(tmask + tb + k)) & 1) A += ph;
+        const ulonglong2 t = tm[k];
+        if (__popcll(gfix & t.x) & 1) A += (U)t.y;
     }
 #pragma unroll
     for (int mu = 1; mu < NR; ++mu) {
         for (int k = op.csr[mu]; k < op.csr[mu + 1]; ++k) {
-            U ph = (U)__ldg(tphi + tb + k);
-            bool c = __popcll(gfix & __ldg(tmask + tb + k)) & 1;
+            const ulonglong2 t = tm[k];
+            const U ph = (U)t.y;
+            const bool c = __popcll(gfix & t.x) & 1;
             A += c ? ph : (U)0;
             C[mu] += c ? (U)(0 - ph) : ph;
         }
@@ -275,13 +278,35 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     // complex64 threads move adjacent pairs in the load/store phases
     constexpr int NROW = kC128 ? NR : NR / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
     const PassDesc &d = args.d;
     const int L = d.L;
     const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
     C2 *state = reinterpret_cast<C2 *>(args.state);
     C2 *snap = reinterpret_cast<C2 *>(args.snap);
     const uint32_t flags = d.flags;
+
+    // the pass's program into shared memory (ops, matrices, diagonal terms)
+    unsigned char *pbase = smem_raw + (sizeof(C2) << L);
+    DevOp *sops = reinterpret_cast<DevOp *>(pbase);
+    C2 *smats = reinterpret_cast<C2 *>(pbase + (size_t)d.nops * sizeof(DevOp));
+    uint64_t *sterms = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(smats) +
+                                                    (size_t)d.nmat * 16 * sizeof(C2));
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(args.ops + d.op0);
+        int4 *dst = reinterpret_cast<int4 *>(sops);
+        for (uint32_t i = tid; i < d.nops * (uint32_t)(sizeof(DevOp) / 16); i += nthr) dst[i] = src[i];
+        const int4 *msrc = kC128 ? reinterpret_cast<const int4 *>(args.mats + 32 * (size_t)d.mat0)
+                                 : reinterpret_cast<const int4 *>(args.matsf + 32 * (size_t)d.mat0);
+        int4 *mdst = reinterpret_cast<int4 *>(smats);
+        for (uint32_t i = tid; i < d.nmat * (uint32_t)(16 * sizeof(C2) / 16); i += nthr) mdst[i] = msrc[i];
+        for (uint32_t i = tid; i < d.nterm; i += nthr) {
+            sterms[2 * i] = args.tmask[d.term0 + i];
+            sterms[2 * i + 1] = args.tphi[d.term0 + i];
+        }
+    }
+    const SProg<R> P{sops, smats, sterms, d.op0, d.mat0, d.term0};
 
     // this thread's part of a load row (local index tid, or 2 tid for pairs)
     const uint32_t erow = kC128 ? (uint32_t)tid : (uint32_t)tid << 1;
@@ -290,6 +315,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         if (erow >> b & 1) gthr |= 1ull << d.win[b];
     const uint32_t sthr = tile_swizzle(erow, kC128);
     const float wleaf = (float)d.leaf_w;
+    __syncthreads();
 
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
 
@@ -298,42 +324,56 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         for (int b = 0; b < d.n_cw; ++b)
             if (t >> b & 1) tb |= 1ull << d.cw[b];
         const uint64_t gbase = tb | gthr;
-        // load the tile (16-byte accesses)
+        // load the tile: every row load in flight before the shared stores
         if constexpr (kC128) {
+            C2 buf[NROW];
 #pragma unroll
-            for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = state[gbase | d.grow[i]];
+            for (int i = 0; i < NROW; ++i) buf[i] = state[gbase | d.grow[i]];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = buf[i];
         } else {
             const float4 *src = reinterpret_cast<const float4 *>(state);
             float4 *dst = reinterpret_cast<float4 *>(tile);
+            float4 buf[NROW];
 #pragma unroll
-            for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = src[(gbase | d.grow[i]) >> 1];
+            for (int i = 0; i < NROW; ++i) buf[i] = src[(gbase | d.grow[i]) >> 1];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
         for (int s = 0; s < d.n_stages; ++s) {
             const StageDesc &sd = d.st[s];
-            if (sd.op_count == 0) continue;
-            // thread bits -> the stage's non-register local bits
-            uint32_t e = 0;
-            uint64_t gfix = tb;
-            for (int b = 0; b < L - V; ++b)
-                if (tid >> b & 1) {
-                    e |= 1u << sd.cpos[b];
-                    gfix |= 1ull << d.win[sd.cpos[b]];
-                }
+            // thread bits -> the stage's non-register local bits: insert a zero
+            // at each register bit (ascending)
+            uint32_t e = (uint32_t)tid;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const uint32_t rb = sd.rbits[i];
+                e = ((e >> rb) << (rb + 1)) | (e & ((1u << rb) - 1u));
+            }
             const uint32_t sb = tile_swizzle(e, kC128);
             C2 a[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) a[r] = tile[sb ^ sd.sr[r]];
+            bool have_gfix = false;
+            uint64_t gfix = 0;
             for (uint32_t k = 0; k < sd.op_count; ++k) {
-                const DevOp &op = args.ops[sd.op_begin + k];
+                const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
                 const int type = op.type;
                 if (type == OP_MAT1) {
-                    dispatch1<V>(a, op.a, op.sub, mat_at<R>(args, op.mat, 0), mat_at<R>(args, op.mat, 1),
-                                 mat_at<R>(args, op.mat, 2), mat_at<R>(args, op.mat, 3));
+                    dispatch1<V>(a, op.a, op.sub, P.mat(op.mat, 0), P.mat(op.mat, 1), P.mat(op.mat, 2),
+                                 P.mat(op.mat, 3));
                 } else if (type == OP_MAT2) {
-                    dispatch2<V>(a, op, args);
+                    dispatch2<V, R>(a, op, P);
                 } else {
-                    apply_diag<R, V>(a, op, args.tmask, args.tphi, gfix);
+                    if (!have_gfix) {
+                        // global index of this thread's register 0
+                        gfix = tb;
+                        for (int b = 0; b < L; ++b)
+                            if (e >> b & 1) gfix |= 1ull << d.win[b];
+                        have_gfix = true;
+                    }
+                    apply_diag<R, V>(a, op, P, gfix);
                 }
             }
 #pragma unroll
@@ -343,10 +383,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         // store + epilogue
         float pn = 0.f, pr = 0.f, pi = 0.f;
         double dn = 0.0, dr = 0.0, di = 0.0;
+        if constexpr (kC128) {
 #pragma unroll
-        for (int i = 0; i < NROW; ++i) {
-            const uint64_t g = gbase | d.grow[i];
-            if constexpr (kC128) {
+            for (int i = 0; i < NROW; ++i) {
+                const uint64_t g = gbase | d.grow[i];
                 C2 v = tile[sthr ^ d.srow[i]];
                 if (flags & PF_WRITE) state[g] = v;
                 if (flags & PF_SNAPSHOT) snap[g] = v;
@@ -357,23 +397,37 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
                     dr += h * v.x;
                     di += h * v.y;
                 }
-            } else {
-                const float4 v = reinterpret_cast<const float4 *>(tile)[(sthr ^ d.srow[i]) >> 1];
-                if (flags & PF_WRITE) reinterpret_cast<float4 *>(state)[g >> 1] = v;
-                if (flags & PF_SNAPSHOT) reinterpret_cast<float4 *>(snap)[g >> 1] = v;
-                if (flags & PF_LEAF) {
-                    double2 *ap = reinterpret_cast<double2 *>(args.acc) + (g >> 1);
-                    double2 acc = *ap;
-                    acc.x = leaf_add(acc.x, wleaf * fmaf(v.x, v.x, v.y * v.y));
-                    acc.y = leaf_add(acc.y, wleaf * fmaf(v.z, v.z, v.w * v.w));
-                    *ap = acc;
+            }
+        } else {
+            const float4 *ts = reinterpret_cast<const float4 *>(tile);
+            if (flags & PF_LEAF) {
+                // every accumulator load in flight before the updates
+                double2 *accp = reinterpret_cast<double2 *>(args.acc);
+                double2 ab[NROW];
+#pragma unroll
+                for (int i = 0; i < NROW; ++i) ab[i] = accp[(gbase | d.grow[i]) >> 1];
+#pragma unroll
+                for (int i = 0; i < NROW; ++i) {
+                    const float4 v = ts[(sthr ^ d.srow[i]) >> 1];
+                    ab[i].x = leaf_add(ab[i].x, wleaf * fmaf(v.x, v.x, v.y * v.y));
+                    ab[i].y = leaf_add(ab[i].y, wleaf * fmaf(v.z, v.z, v.w * v.w));
+                    accp[(gbase | d.grow[i]) >> 1] = ab[i];
                 }
-                if (flags & PF_REDUCE) {
-                    const float h0 = check_sign(g), h1 = check_sign(g | 1);
-                    pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
-                    pn = fmaf(v.z, v.z, fmaf(v.w, v.w, pn));
-                    pr = fmaf(h0, v.x, fmaf(h1, v.z, pr));
-                    pi = fmaf(h0, v.y, fmaf(h1, v.w, pi));
+            }
+            if (flags & (PF_WRITE | PF_SNAPSHOT | PF_REDUCE)) {
+#pragma unroll
+                for (int i = 0; i < NROW; ++i) {
+                    const uint64_t g = gbase | d.grow[i];
+                    const float4 v = ts[(sthr ^ d.srow[i]) >> 1];
+                    if (flags & PF_WRITE) reinterpret_cast<float4 *>(state)[g >> 1] = v;
+                    if (flags & PF_SNAPSHOT) reinterpret_cast<float4 *>(snap)[g >> 1] = v;
+                    if (flags & PF_REDUCE) {
+                        const float h0 = check_sign(g), h1 = check_sign(g | 1);
+                        pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
+                        pn = fmaf(v.z, v.z, fmaf(v.w, v.w, pn));
+                        pr = fmaf(h0, v.x, fmaf(h1, v.z, pr));
+                        pi = fmaf(h0, v.y, fmaf(h1, v.w, pi));
+                    }
                 }
             }
         }
@@ -392,7 +446,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             red_r += __shfl_down_sync(0xffffffffu, red_r, off);
             red_i += __shfl_down_sync(0xffffffffu, red_i, off);
         }
-        const int warp = tid >> 5, lane = tid & 31, nw = (blockDim.x + 31) >> 5;
+        const int warp = tid >> 5, lane = tid & 31, nw = (nthr + 31) >> 5;
         if (lane == 0) { wsum[0][warp] = red_n; wsum[1][warp] = red_r; wsum[2][warp] = red_i; }
         __syncthreads();
         if (tid == 0) {
@@ -476,7 +530,7 @@ static cudaError_t allow_smem(size_t smem) {
 
 template <typename R, int V>
 static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
-    const size_t smem = (sizeof(R) * 2) << a.d.L;
+    const size_t smem = ((sizeof(R) * 2) << a.d.L) + a.d.prog_bytes;
     const int threads = 1 << (a.d.L - V);
     cudaError_t e = allow_smem<R, V>(smem);
     if (e != cudaSuccess) return e;
@@ -486,7 +540,7 @@ static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
 
 template <typename R, int V>
 static int occupancy_t(int L) {
-    const size_t smem = (sizeof(R) * 2) << L;
+    const size_t smem = ((sizeof(R) * 2) << L) + kMaxPassProgramBytes;
     const int threads = 1 << (L - V);
     int nb = 0;
     if (allow_smem<R, V>(smem) != cudaSuccess) return 1;

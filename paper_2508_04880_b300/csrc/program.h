@@ -60,9 +60,16 @@ struct StageDesc {
     uint8_t rbits[8];      // local bit positions held in registers (ascending)
     uint8_t cpos[16];      // remaining local bit positions (ascending) -> thread bits
     uint16_t sr[32];       // swizzled shared-memory offset of register index r
+    uint16_t sw1[8];       // swizzled offset of each register bit alone (sr is their xor)
     uint64_t greg[8];      // global bit of each register bit (1 << win[rbits[i]])
     uint32_t op_begin, op_count;
 };
+
+// Per-pass program limits: a pass's ops, matrices and diagonal terms are
+// copied into shared memory next to the tile.
+constexpr int kMaxStageOps = 48;
+constexpr int kMaxDiagTerms = 256;
+constexpr uint32_t kMaxPassProgramBytes = 40 * 1024;
 
 enum PassFlags : uint32_t {
     PF_WRITE = 1,          // write the tile back to the state
@@ -84,7 +91,10 @@ struct PassDesc {
     StageDesc st[kMaxStages];
     double leaf_w;
     int32_t snap;          // snapshot slot for PF_SNAPSHOT
-    int32_t pad;
+    uint32_t prog_bytes;   // shared-memory bytes of the program below
+    uint32_t op0, nops;    // the pass's ops: [op0, op0 + nops) of Program::ops
+    uint32_t mat0, nmat;   // its matrix slots
+    uint32_t term0, nterm; // its diagonal terms
 };
 
 // Host-side step of the traversal.

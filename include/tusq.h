@@ -195,6 +195,8 @@ typedef struct {
     double drift_tol;         /* drift check threshold (1e-6); < 0 disables checks */
     uint64_t snapshot_bytes;  /* device budget for LIFO branch snapshots */
     int check_every;          /* reserved, 0 */
+    int schedule;             /* fusion: 0 = grow windows by the op that admits most
+                                 further ops (default), 1 = in list order */
 } tusq_run_opts;
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
@@ -215,6 +217,10 @@ typedef struct {
     double state_bytes;           /* bytes of one state */
     double algorithmic_bytes;     /* HBM bytes the passes must move (reads + writes) */
     double program_bytes;         /* device program copied host->device at create */
+    uint64_t stages;              /* register stages over all passes */
+    uint64_t matrix_ops;          /* fused 2x2 / 4x4 device ops */
+    uint64_t diag_ops;            /* fused diagonal-phase device ops */
+    uint64_t diag_terms;          /* their terms */
 } tusq_run_info_t;
 
 /* Compile a plan into a device program for the current device and allocate
@@ -253,6 +259,12 @@ int tusq_compile_stats(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run
 int tusq_exec_set_profiling(tusq_exec *e, int on);
 int tusq_exec_pass_profile(tusq_exec *e, uint64_t *n_passes, const float **ms,
                            const double **bytes);
+
+/* Structure of every pass of the compiled program, in launch order, 8
+ * integers per pass: register stages, ops, 2x2 ops, 4x4 ops, diagonal ops,
+ * diagonal terms, flags (1 write, 2 snapshot, 4 leaf, 8 reduce), tile
+ * qubits.  Borrowed, valid until tusq_exec_free. */
+int tusq_exec_pass_structure(tusq_exec *e, uint64_t *n_passes, const int32_t **fields);
 
 /* Host hook for tests: add `delta` to the recorded norm of every record
  * taken from now on (0 = off).  Forces the drift path without touching the

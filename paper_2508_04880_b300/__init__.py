@@ -35,7 +35,7 @@ EXPORTS = [
     "tusq_plan_n_qubits", "tusq_plan_shard", "tusq_plan_free", "tusq_run_opts_default",
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
-    "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_free",
+    "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
     "tusq_run", "tusq_run_noalloc", "tusq_server_create", "tusq_submit", "tusq_poll", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
@@ -67,7 +67,8 @@ class PlanStats(ctypes.Structure):
 class RunOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_window", ctypes.c_int), ("traversal", ctypes.c_int),
                 ("leaf_peek", ctypes.c_int), ("root_reset", ctypes.c_int), ("drift_tol", ctypes.c_double),
-                ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int)]
+                ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):
@@ -75,7 +76,8 @@ class RunInfo(ctypes.Structure):
         "passes", "gate_apps", "pauli_apps", "leaf_passes", "checks", "restores", "unrecovered",
         "resets", "kernel_launches")] + \
         [(f, ctypes.c_double) for f in ("max_drift", "state_bytes", "algorithmic_bytes",
-                                        "program_bytes")]
+                                        "program_bytes")] + \
+        [(f, ctypes.c_uint64) for f in ("stages", "matrix_ops", "diag_ops", "diag_terms")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -112,6 +114,7 @@ def _load():
         "tusq_compile_stats": (i32, [vp, P(RunOpts), P(RunInfo)]),
         "tusq_exec_set_profiling": (i32, [vp, i32]),
         "tusq_exec_pass_profile": (i32, [vp, P(u64), P(P(ctypes.c_float)), P(P(f64))]),
+        "tusq_exec_pass_structure": (i32, [vp, P(u64), P(P(ctypes.c_int32))]),
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
@@ -323,6 +326,16 @@ class Exec:
 
     def set_profiling(self, on: bool) -> None:
         _check(lib.tusq_exec_set_profiling(self.h, int(bool(on))))
+
+    def pass_structure(self) -> np.ndarray:
+        """Per pass (launch order): stages, ops, 2x2 ops, 4x4 ops, diagonal
+        ops, diagonal terms, flags, tile qubits."""
+        n = ctypes.c_uint64()
+        f = ctypes.POINTER(ctypes.c_int32)()
+        _check(lib.tusq_exec_pass_structure(self.h, ctypes.byref(n), ctypes.byref(f)))
+        if n.value == 0:
+            return np.zeros((0, 8), np.int32)
+        return np.ctypeslib.as_array(f, (n.value * 8,)).copy().reshape(-1, 8)
 
     def pass_profile(self):
         """(ms per pass, algorithmic bytes per pass) of the last launch."""

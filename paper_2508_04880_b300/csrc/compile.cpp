@@ -148,7 +148,8 @@ struct Pass {
 // group (found by trying each candidate on a copy of the DAG state).
 template <class QubitsOf>
 std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uint64_t forced,
-                                       QubitsOf qubits_of, std::vector<uint64_t> *wins) {
+                                       QubitsOf qubits_of, std::vector<uint64_t> *wins,
+                                       bool lookahead = true) {
     const int m = (int)ops.size();
     std::vector<std::vector<int>> succ(m);
     std::vector<int> indeg(m, 0);
@@ -209,6 +210,10 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
                 if (__builtin_popcountll(W | q) > cap) continue;
                 if (std::find(tried.begin(), tried.end(), q) != tried.end()) continue;
                 tried.push_back(q);
+                if (!lookahead) {   // list order: the first blocked op that fits
+                    if (best < 0 || b < best) { best = b; best_q = q; }
+                    continue;
+                }
                 std::vector<int> deg2 = indeg;
                 std::vector<char> dn2 = done;
                 std::vector<int> rdy2 = ready;
@@ -326,6 +331,7 @@ struct Encoder {
     bool c128;
     int V;
     int Lmax;
+    bool lookahead = true;
 
     // Encode one pass (window + ops already in application order) into
     // PassDescs: several when the register stages exceed kMaxStages or the
@@ -350,21 +356,58 @@ struct Encoder {
         const int v = std::min(V, L);
         std::vector<uint64_t> swin;
         std::vector<std::vector<int>> sched;
-        if (!ops.empty()) sched = schedule(ops, v, 0, lq, &swin);
-        // stage pieces of at most kMaxStageOps ops (a long stage is cut into
-        // several with the same register bits)
-        struct Piece { uint64_t R; std::vector<int> ops; };
+        if (!ops.empty()) sched = schedule(ops, v, 0, lq, &swin, lookahead);
+        // inside a stage, order the ops so that every diagonal op that is ready
+        // at the same time is applied together (alternately all ready diagonal
+        // ops, then all ready matrix ops), and merge neighbours: each diagonal
+        // run costs a Walsh transform and a phase per amplitude
+        struct Piece { uint64_t R; std::vector<HOp> ops; };
         std::vector<Piece> pieces;
-        for (size_t s = 0; s < sched.size(); ++s)
-            for (size_t k = 0; k < sched[s].size(); k += kMaxStageOps)
-                pieces.push_back(Piece{swin[s], std::vector<int>(sched[s].begin() + k,
-                    sched[s].begin() + std::min(sched[s].size(), k + (size_t)kMaxStageOps))});
+        for (size_t s = 0; s < sched.size(); ++s) {
+            const std::vector<int> &g = sched[s];
+            const int m = (int)g.size();
+            std::vector<int> indeg(m, 0);
+            std::vector<std::vector<int>> succ(m);
+            for (int b = 0; b < m; ++b)
+                for (int a = 0; a < b; ++a) {
+                    const HOp &x = ops[g[a]], &y = ops[g[b]];
+                    if (x.type == H_DIAG && y.type == H_DIAG) continue;
+                    if (x.qmask() & y.qmask()) { succ[a].push_back(b); indeg[b]++; }
+                }
+            std::vector<HOp> ordered;
+            std::vector<char> done(m, 0);
+            int left = m;
+            bool diag_phase = true;
+            while (left > 0) {
+                bool progress = true;
+                int taken = 0;
+                while (progress) {
+                    progress = false;
+                    for (int b = 0; b < m; ++b) {
+                        if (done[b] || indeg[b] != 0) continue;
+                        if ((ops[g[b]].type == H_DIAG) != diag_phase) continue;
+                        done[b] = 1;
+                        --left;
+                        ++taken;
+                        ordered.push_back(ops[g[b]]);
+                        for (int c : succ[b]) indeg[c]--;
+                        progress = true;
+                    }
+                }
+                diag_phase = !diag_phase;
+                (void)taken;
+            }
+            std::vector<HOp> merged = merge_ops(ordered);
+            for (size_t k = 0; k < merged.size(); k += kMaxStageOps)
+                pieces.push_back(Piece{swin[s], std::vector<HOp>(merged.begin() + k,
+                    merged.begin() + std::min(merged.size(), k + (size_t)kMaxStageOps))});
+        }
         const uint32_t mat_bytes = c128 ? 256 : 128;
         auto piece_bytes = [&](const Piece &pc) {
             uint32_t b = 0;
-            for (int oi : pc.ops) {
+            for (const HOp &o : pc.ops) {
                 b += sizeof(DevOp);
-                if (ops[oi].type == H_DIAG) b += 16 * (uint32_t)ops[oi].terms.size();
+                if (o.type == H_DIAG) b += 16 * (uint32_t)o.terms.size();
                 else b += mat_bytes;
             }
             return b;
@@ -435,8 +478,7 @@ struct Encoder {
                 for (int i = 0; i < 64; ++i) regidx[i] = -1;
                 for (int i = 0; i < v; ++i) regidx[sd.rbits[i]] = i;
                 sd.op_begin = (uint32_t)prog.ops.size();
-                for (int oi : pieces[s].ops) {
-                    const HOp &o = ops[oi];
+                for (const HOp &o : pieces[s].ops) {
                     if (last && last_uids) {
                         last_uids->push_back(o.uid);
                         last_uids->insert(last_uids->end(), o.merged.begin(), o.merged.end());
@@ -535,6 +577,7 @@ struct Compiler {
         if (co.max_window > 0) lmax = std::min(co.max_window, lmax);
         L = std::min(lmax, n);
         enc.Lmax = L;
+        enc.lookahead = co.schedule == 0;
         // the lowest qubits stay in every window (contiguous 128-byte runs),
         // leaving room for any two-qubit gate
         int nf = std::min(co.precision == TUSQ_C128 ? 3 : 4, std::max(L - 2, 0));
@@ -583,7 +626,7 @@ struct Compiler {
         std::vector<uint64_t> wins;
         auto gq = [](const HOp &o) { return o.type == H_DIAG ? 0ULL : o.qmask(); };
         std::vector<std::vector<int>> groups;
-        if (!ops.empty()) groups = schedule(ops, L, forced, gq, &wins);
+        if (!ops.empty()) groups = schedule(ops, L, forced, gq, &wins, co.schedule == 0);
         if (groups.empty()) {
             // nothing to apply: an empty pass carries the flags
             std::vector<int> win;

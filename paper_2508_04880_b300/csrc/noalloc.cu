@@ -163,6 +163,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
     co.traversal = o.traversal;
     co.leaf_peek = o.leaf_peek;
     co.root_reset = o.root_reset;
+    co.schedule = o.schedule;
     co.checks = o.drift_tol >= 0 && o.traversal != TUSQ_FROM_SCRATCH;
     const bool want_snaps = co.checks || o.traversal == TUSQ_DFTT_SNAPSHOT;
     uint64_t budget = o.snapshot_bytes ? o.snapshot_bytes : 8 * state_bytes;

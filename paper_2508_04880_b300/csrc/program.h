@@ -155,6 +155,7 @@ struct CompileOpts {
     int root_reset;
     bool checks;
     int snapshots;         // snapshot slots available
+    int schedule;          // 0 lookahead window growth, 1 list order
 };
 
 }  // namespace tusq

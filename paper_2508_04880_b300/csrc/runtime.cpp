@@ -60,6 +60,7 @@ struct tusq_exec {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<float> prof_ms;
     std::vector<double> prof_bytes;
+    std::vector<int32_t> structure;   // 8 fields per pass in launch order
 };
 
 namespace {
@@ -111,6 +112,7 @@ static CompileOpts compile_opts_of(const tusq_run_opts *o, size_t state_bytes) {
     co.traversal = o->traversal;
     co.leaf_peek = o->leaf_peek;
     co.root_reset = o->root_reset;
+    co.schedule = o->schedule;
     co.checks = o->drift_tol >= 0 && o->traversal != TUSQ_FROM_SCRATCH;
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
@@ -148,7 +150,14 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
     for (const Step &s : pg.steps) {
         ++launches;
         if (s.type == ST_PASS) {
-            bytes += pass_bytes(pg.passes[s.pass], sb, dim);
+            const PassDesc &d = pg.passes[s.pass];
+            bytes += pass_bytes(d, sb, dim);
+            info->stages += d.n_stages;
+            info->diag_terms += d.nterm;
+            for (uint32_t k = 0; k < d.nops; ++k) {
+                if (pg.ops[d.op0 + k].type == OP_DIAG) info->diag_ops++;
+                else info->matrix_ops++;
+            }
         } else if (s.type == ST_INIT) {
             bytes += sb;
         } else if (s.type == ST_RESTORE && s.check < 0) {
@@ -445,6 +454,26 @@ int tusq_exec_finish(tusq_exec *e, tusq_run_info_t *info) {
 int tusq_exec_set_profiling(tusq_exec *e, int on) {
     if (!e) { set_error("tusq_exec_set_profiling: NULL exec"); return TUSQ_EINVAL; }
     e->profiling = on != 0;
+    return TUSQ_OK;
+}
+
+int tusq_exec_pass_structure(tusq_exec *e, uint64_t *n_passes, const int32_t **fields) {
+    if (!e || !n_passes) { set_error("tusq_exec_pass_structure: NULL argument"); return TUSQ_EINVAL; }
+    if (e->structure.empty()) {
+        const Program &pg = e->prog;
+        for (const Step &s : pg.steps) {
+            if (s.type != ST_PASS) continue;
+            const PassDesc &d = pg.passes[s.pass];
+            int32_t f[8] = {d.n_stages, (int32_t)d.nops, 0, 0, 0, (int32_t)d.nterm, (int32_t)d.flags, d.L};
+            for (uint32_t k = 0; k < d.nops; ++k) {
+                int t = pg.ops[d.op0 + k].type;
+                f[t == OP_MAT1 ? 2 : t == OP_MAT2 ? 3 : 4]++;
+            }
+            e->structure.insert(e->structure.end(), f, f + 8);
+        }
+    }
+    *n_passes = e->structure.size() / 8;
+    if (fields) *fields = e->structure.data();
     return TUSQ_OK;
 }
 

@@ -155,6 +155,7 @@ extern "C" int emu_run(const tusq_plan_t *p, const tusq_run_opts *o, double *pro
     co.traversal = o->traversal;
     co.leaf_peek = o->leaf_peek;
     co.root_reset = o->root_reset;
+    co.schedule = o->schedule;
     co.checks = o->drift_tol >= 0 && o->traversal != TUSQ_FROM_SCRATCH;
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;

@@ -277,6 +277,34 @@ void tusq_exec_free(tusq_exec *e);
 int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
              void *cuda_stream);
 
+/* ------------------------------------------------------- batched jobs */
+
+typedef struct tusq_batch tusq_batch;   /* opaque */
+
+/* Many small jobs in one launch (the batching of Sec. III-B's traversal
+ * across independent noisy simulations): each CTA of one persistent kernel
+ * takes jobs from a work queue and runs a job's whole traversal with its
+ * state held in shared memory -- jobs of 5..13 qubits (complex64) or 4..12
+ * (complex128), of uneven depth and tree shape.  probs_dev[j] is job j's
+ * caller-owned device output (2^n_j doubles, zeroed by the kernel).
+ * use_graph != 0 records the launch into a CUDA graph on the first
+ * tusq_batch_launch and replays it afterwards (needs a non-default stream).
+ * Options as tusq_run (leaf peek is not used: the state never leaves the
+ * CTA).  Plans and outputs must stay alive while the batch exists. */
+int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *opts,
+                      double *const *probs_dev, int use_graph, void *cuda_stream, tusq_batch **out);
+int tusq_batch_launch(tusq_batch *b, void *cuda_stream);
+/* Synchronises; *info (optional) gets the summed counters of all jobs. */
+int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info);
+void tusq_batch_free(tusq_batch *b);
+
+/* Autotuner: times one batch launch for each traversal policy and fusion
+ * schedule (starting from *base) and returns the fastest options in *best
+ * (and its time in *best_ms). */
+int tusq_batch_autotune(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *base,
+                        double *const *probs_dev, void *cuda_stream, tusq_run_opts *best,
+                        double *best_ms);
+
 /* ------------------------------------------------- allocation-free run */
 
 /* Size of the static device scratch used by tusq_run_noalloc (32 MiB). */

@@ -36,7 +36,9 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
-    "tusq_run", "tusq_run_noalloc", "tusq_server_create", "tusq_submit", "tusq_poll", "tusq_server_drain",
+    "tusq_run", "tusq_run_noalloc", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
+    "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
+    "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
 
@@ -118,6 +120,11 @@ def _load():
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
+        "tusq_batch_create": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), i32, vp, P(vp)]),
+        "tusq_batch_launch": (i32, [vp, vp]),
+        "tusq_batch_finish": (i32, [vp, P(RunInfo)]),
+        "tusq_batch_free": (None, [vp]),
+        "tusq_batch_autotune": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), vp, P(RunOpts), P(f64)]),
         "tusq_server_create": (i32, [ctypes.c_size_t, i32, P(vp)]),
         "tusq_submit": (i32, [vp, vp, P(RunOpts), vp, P(u64)]),
         "tusq_poll": (i32, [vp, u64, P(i32), P(f64)]),
@@ -386,6 +393,54 @@ def run_torch(plan: Plan, opts: Optional[RunOpts] = None, device: str = "cuda"):
     ex.launch(probs.data_ptr(), stream)
     info = ex.finish()
     return probs, info
+
+
+# ------------------------------------------------------------------ batching
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(p) for p in ptrs])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+class Batch:
+    """Owns a tusq_batch: many small jobs (5..13 qubits complex64, 4..12
+    complex128) traversed by one persistent launch, optionally replayed from
+    a captured CUDA graph."""
+
+    def __init__(self, plans, probs_ptrs, opts: Optional[RunOpts] = None, use_graph: bool = False,
+                 stream: int = 0):
+        self.plans = list(plans)
+        self.opts = opts or run_opts()
+        pp, self._pa = _ptr_array([p.h.value for p in self.plans])
+        op, self._oa = _ptr_array(list(probs_ptrs))
+        h = ctypes.c_void_p()
+        _check(lib.tusq_batch_create(pp, len(self.plans), ctypes.byref(self.opts), op, int(bool(use_graph)),
+                                     ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream: int = 0) -> None:
+        _check(lib.tusq_batch_launch(self.h, ctypes.c_void_p(stream)))
+
+    def finish(self) -> dict:
+        info = RunInfo()
+        _check(lib.tusq_batch_finish(self.h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.tusq_batch_free(self.h)
+            self.h = None
+
+
+def tusq_batch_autotune(plans, probs_ptrs, base: Optional[RunOpts] = None, stream: int = 0):
+    """Fastest (traversal, schedule) for this batch: returns (RunOpts, ms)."""
+    pp, _pa = _ptr_array([p.h.value for p in plans])
+    op, _oa = _ptr_array(list(probs_ptrs))
+    best = RunOpts()
+    ms = ctypes.c_double()
+    _check(lib.tusq_batch_autotune(pp, len(plans), ctypes.byref(base or run_opts()), op, ctypes.c_void_p(stream),
+                                   ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
 
 
 # ------------------------------------------------------------------- serving

@@ -1,0 +1,382 @@
+// Batched execution of many small jobs in one launch (the job kernel), with
+// optional CUDA-graph replay and an autotuner over compile options.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+#include "program.h"
+
+namespace tusq {
+void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, cudaStream_t st);
+int job_max_qubits_of(int precision);
+int job_occupancy(int precision);
+}  // namespace tusq
+
+using namespace tusq;
+
+struct tusq_batch {
+    int precision = TUSQ_C64;
+    double drift_tol = 1e-6;
+    int n_jobs = 0;
+    int grid = 1;
+    std::vector<JobDesc> jobs;
+    Program totals;                     // summed counters of the jobs' programs
+    uint64_t launches_per_run = 1;
+    // device buffers
+    JobDesc *d_jobs = nullptr;
+    Step *d_steps = nullptr;
+    PassDesc *d_passes = nullptr;
+    DevOp *d_ops = nullptr;
+    double *d_mats = nullptr;
+    float *d_matsf = nullptr;
+    uint64_t *d_tmask = nullptr, *d_tphi = nullptr;
+    unsigned char *d_snaps = nullptr;
+    double *d_records = nullptr;
+    unsigned int *d_next = nullptr;
+    unsigned long long *d_counters = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool use_graph = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+#define B_TRY(call)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            set_error(std::string("batch: ") + #call + ": " + cudaGetErrorString(e_)); \
+            return TUSQ_ECUDA;                                                        \
+        }                                                                             \
+    } while (0)
+
+template <class T>
+int upload(T **dst, const std::vector<T> &v, cudaStream_t st) {
+    size_t bytes = std::max<size_t>(sizeof(T) * v.size(), 16);
+    B_TRY(cudaMallocAsync((void **)dst, bytes, st));
+    if (!v.empty()) B_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+    return TUSQ_OK;
+}
+
+void free_batch_buffers(tusq_batch *b, cudaStream_t st) {
+    void *bufs[] = {b->d_jobs, b->d_steps, b->d_passes, b->d_ops, b->d_mats, b->d_matsf, b->d_tmask,
+                    b->d_tphi, b->d_snaps, b->d_records, b->d_next, b->d_counters};
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, st);
+}
+
+int run_once(tusq_batch *b, cudaStream_t st) {
+    BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.jobs = b->d_jobs;
+    a.n_jobs = b->n_jobs;
+    a.steps = b->d_steps;
+    a.passes = b->d_passes;
+    a.ops = b->d_ops;
+    a.mats = b->d_mats;
+    a.matsf = b->d_matsf;
+    a.tmask = b->d_tmask;
+    a.tphi = b->d_tphi;
+    a.next_job = b->d_next;
+    a.counters = b->d_counters;
+    a.drift_tol = b->drift_tol;
+    B_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int), st));
+    B_TRY(cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    B_TRY(launch_jobs(a, b->precision, b->grid, st));
+    return TUSQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *opts,
+                      double *const *probs_dev, int use_graph, void *cuda_stream, tusq_batch **out) {
+    if (!plans || !probs_dev || !out || n_jobs == 0) {
+        set_error("tusq_batch_create: NULL argument or no jobs");
+        return TUSQ_EINVAL;
+    }
+    tusq_run_opts o;
+    tusq_run_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != TUSQ_C64 && o.precision != TUSQ_C128) {
+        set_error("tusq_batch_create: bad precision");
+        return TUSQ_EINVAL;
+    }
+    if (o.traversal < TUSQ_DFTT || o.traversal > TUSQ_DFTT_SNAPSHOT) {
+        set_error("tusq_batch_create: bad traversal");
+        return TUSQ_EINVAL;
+    }
+    const int vbits = o.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64;
+    const int nmax = job_max_qubits_of(o.precision);
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        if (!plans[j] || !probs_dev[j]) {
+            set_error("tusq_batch_create: NULL plan or output");
+            return TUSQ_EINVAL;
+        }
+        if (plans[j]->n < vbits || plans[j]->n > nmax) {
+            set_error("tusq_batch_create: job " + std::to_string(j) + " has " + std::to_string(plans[j]->n) +
+                      " qubits; batched jobs need " + std::to_string(vbits) + ".." + std::to_string(nmax));
+            return TUSQ_EINVAL;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    tusq_batch *b = new (std::nothrow) tusq_batch;
+    if (!b) {
+        set_error("tusq_batch_create: out of host memory");
+        return TUSQ_ENOMEM;
+    }
+    b->precision = o.precision;
+    b->drift_tol = o.drift_tol;
+    b->n_jobs = (int)n_jobs;
+    b->use_graph = use_graph != 0;
+    const size_t amp = o.precision == TUSQ_C128 ? 16 : 8;
+    std::vector<Step> steps;
+    std::vector<PassDesc> passes;
+    std::vector<DevOp> ops;
+    std::vector<double> mats;
+    std::vector<float> matsf;
+    std::vector<uint64_t> tmask, tphi;
+    std::vector<size_t> snap_off, rec_off;
+    size_t snap_bytes = 0, rec_count = 0;
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        const tusq_plan_t &P = *plans[j];
+        const size_t state = amp << P.n;
+        CompileOpts co;
+        co.precision = o.precision;
+        co.max_window = 0;
+        co.traversal = o.traversal;
+        co.leaf_peek = 0;              // the state lives in shared memory: leaf passes keep their result
+        co.root_reset = o.root_reset;
+        co.schedule = o.schedule;
+        co.checks = o.drift_tol >= 0 && o.traversal != TUSQ_FROM_SCRATCH;
+        const uint64_t budget = o.snapshot_bytes ? o.snapshot_bytes : 8 * state;
+        co.snapshots = (co.checks || o.traversal == TUSQ_DFTT_SNAPSHOT) ? (int)std::min<uint64_t>(budget / state, 64) : 0;
+        Program pg;
+        try {
+            compile_program(P, co, pg);
+        } catch (const std::exception &ex) {
+            delete b;
+            set_error(std::string("tusq_batch_create: schedule compilation failed: ") + ex.what());
+            return TUSQ_EINVAL;
+        }
+        // relocate the job's program into the batch arrays
+        const uint32_t pass_base = (uint32_t)passes.size(), op_base = (uint32_t)ops.size();
+        const uint32_t mat_base = (uint32_t)(mats.size() / 32), term_base = (uint32_t)tmask.size();
+        JobDesc jd;
+        std::memset(&jd, 0, sizeof jd);
+        jd.step0 = (uint32_t)steps.size();
+        jd.nsteps = (uint32_t)pg.steps.size();
+        jd.n = P.n;
+        for (Step s : pg.steps) {
+            if (s.type == ST_PASS) s.pass += (int32_t)pass_base;
+            steps.push_back(s);
+        }
+        for (PassDesc d : pg.passes) {
+            d.op0 += op_base;
+            d.mat0 += mat_base;
+            d.term0 += term_base;
+            for (int s = 0; s < d.n_stages; ++s) d.st[s].op_begin += op_base;
+            passes.push_back(d);
+        }
+        for (DevOp d : pg.ops) {
+            d.mat += mat_base;
+            d.term_begin += term_base;
+            ops.push_back(d);
+        }
+        mats.insert(mats.end(), pg.mats.begin(), pg.mats.end());
+        matsf.insert(matsf.end(), pg.matsf.begin(), pg.matsf.end());
+        tmask.insert(tmask.end(), pg.term_mask.begin(), pg.term_mask.end());
+        tphi.insert(tphi.end(), pg.term_phi.begin(), pg.term_phi.end());
+        const int nsnap = std::min(co.snapshots, pg.max_depth);
+        snap_off.push_back(snap_bytes);
+        snap_bytes += (size_t)nsnap * state;
+        rec_off.push_back(rec_count);
+        rec_count += 4 * (size_t)std::max(pg.max_depth, 1);
+        jd.acc = probs_dev[j];
+        b->jobs.push_back(jd);
+        Program &t = b->totals;
+        t.passes_count += pg.passes_count;
+        t.gate_apps += pg.gate_apps;
+        t.pauli_apps += pg.pauli_apps;
+        t.leaf_passes += pg.leaf_passes;
+        t.resets += pg.resets;
+        t.restores += pg.restores;
+        t.n_checks += pg.n_checks;
+    }
+    int rc;
+    if ((rc = upload(&b->d_steps, steps, st)) || (rc = upload(&b->d_passes, passes, st)) ||
+        (rc = upload(&b->d_ops, ops, st)) || (rc = upload(&b->d_mats, mats, st)) ||
+        (rc = upload(&b->d_matsf, matsf, st)) || (rc = upload(&b->d_tmask, tmask, st)) ||
+        (rc = upload(&b->d_tphi, tphi, st))) {
+        free_batch_buffers(b, st);
+        delete b;
+        return rc;
+    }
+    cudaError_t ce = cudaMallocAsync((void **)&b->d_snaps, std::max<size_t>(snap_bytes, 16), st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_records, sizeof(double) * std::max<size_t>(rec_count, 4), st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_next, 16, st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_counters, 4 * sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) {
+        free_batch_buffers(b, st);
+        delete b;
+        set_error(std::string("tusq_batch_create: device allocation failed: ") + cudaGetErrorString(ce));
+        return ce == cudaErrorMemoryAllocation ? TUSQ_ENOMEM : TUSQ_ECUDA;
+    }
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        b->jobs[j].snaps = b->d_snaps + snap_off[j];
+        b->jobs[j].records = b->d_records + rec_off[j];
+    }
+    if ((rc = upload(&b->d_jobs, b->jobs, st))) {
+        free_batch_buffers(b, st);
+        delete b;
+        return rc;
+    }
+    ce = cudaStreamSynchronize(st);   // the host arrays above are about to go
+    if (ce != cudaSuccess) {
+        free_batch_buffers(b, st);
+        delete b;
+        set_error(std::string("tusq_batch_create: ") + cudaGetErrorString(ce));
+        return TUSQ_ECUDA;
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min<int>((int)n_jobs, nsm * job_occupancy(o.precision)));
+    b->last_stream = st;
+    *out = b;
+    return TUSQ_OK;
+}
+
+int tusq_batch_launch(tusq_batch *b, void *cuda_stream) {
+    if (!b) {
+        set_error("tusq_batch_launch: NULL batch");
+        return TUSQ_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    b->last_stream = st;
+    if (!b->use_graph) return run_once(b, st);
+    if (!st) {
+        set_error("tusq_batch_launch: graph replay needs a non-default stream");
+        return TUSQ_EINVAL;
+    }
+    if (!b->graph || b->graph_stream != st) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        B_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = run_once(b, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (rc) return rc;
+        if (ce != cudaSuccess) {
+            set_error(std::string("tusq_batch_launch: capture failed: ") + cudaGetErrorString(ce));
+            return TUSQ_ECUDA;
+        }
+        ce = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            set_error(std::string("tusq_batch_launch: graph instantiation failed: ") + cudaGetErrorString(ce));
+            return TUSQ_ECUDA;
+        }
+        b->graph_stream = st;
+    }
+    B_TRY(cudaGraphLaunch(b->graph, st));
+    return TUSQ_OK;
+}
+
+int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info) {
+    if (!b) {
+        set_error("tusq_batch_finish: NULL batch");
+        return TUSQ_EINVAL;
+    }
+    B_TRY(cudaStreamSynchronize(b->last_stream));
+    unsigned long long cnt[4] = {0, 0, 0, 0};
+    B_TRY(cudaMemcpy(cnt, b->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        const Program &t = b->totals;
+        info->passes = t.passes_count;
+        info->gate_apps = t.gate_apps;
+        info->pauli_apps = t.pauli_apps;
+        info->leaf_passes = t.leaf_passes;
+        info->checks = t.n_checks;
+        info->restores = t.restores + cnt[0];
+        info->unrecovered = cnt[1];
+        info->resets = t.resets;
+        info->kernel_launches = 1;
+        double md;
+        std::memcpy(&md, &cnt[2], sizeof md);
+        info->max_drift = md;
+    }
+    if (cnt[1]) {
+        set_error("tusq_batch_finish: drift above tolerance at a branch node without a snapshot");
+        return TUSQ_EDRIFT;
+    }
+    return TUSQ_OK;
+}
+
+void tusq_batch_free(tusq_batch *b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    free_batch_buffers(b, b->last_stream);
+    cudaStreamSynchronize(b->last_stream);
+    delete b;
+}
+
+int tusq_batch_autotune(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *base,
+                        double *const *probs_dev, void *cuda_stream, tusq_run_opts *best, double *best_ms) {
+    if (!best) {
+        set_error("tusq_batch_autotune: NULL output");
+        return TUSQ_EINVAL;
+    }
+    tusq_run_opts o;
+    tusq_run_opts_default(&o);
+    if (base) o = *base;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int travs[3] = {TUSQ_DFTT_SNAPSHOT, TUSQ_DFTT, TUSQ_FROM_SCRATCH};
+    double best_t = 1e300;
+    bool found = false;
+    for (int tv : travs)
+        for (int sched = 0; sched < 2; ++sched) {
+            tusq_run_opts c = o;
+            c.traversal = tv;
+            c.schedule = sched;
+            tusq_batch *b = nullptr;
+            int rc = tusq_batch_create(plans, n_jobs, &c, probs_dev, 0, cuda_stream, &b);
+            if (rc) return rc;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            rc = tusq_batch_launch(b, cuda_stream);          // warm-up
+            float ms = 0;
+            if (!rc) {
+                cudaEventRecord(e0, st);
+                rc = tusq_batch_launch(b, cuda_stream);
+                cudaEventRecord(e1, st);
+            }
+            if (!rc) rc = tusq_batch_finish(b, nullptr);
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tusq_batch_free(b);
+            if (rc) return rc;
+            if (ms < best_t) {
+                best_t = ms;
+                *best = c;
+                found = true;
+            }
+        }
+    if (best_ms) *best_ms = best_t;
+    return found ? TUSQ_OK : TUSQ_EINVAL;
+}
+
+}  // extern "C"

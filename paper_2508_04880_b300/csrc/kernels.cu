@@ -270,79 +270,46 @@ __device__ __forceinline__ double f32_to_f64_nonneg(float f) {
 // Leaf update of one output element: acc += w p (p, w in FP32 for complex64).
 __device__ __forceinline__ double leaf_add(double acc, float wp) { return acc + f32_to_f64_nonneg(wp); }
 
-template <typename R, int V>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
+// Copy a pass's program (ops, matrix slots, diagonal terms) into shared
+// memory at pbase; the caller synchronises before use.
+template <typename R>
+__device__ __forceinline__ SProg<R> load_program(const PassDesc &d, unsigned char *pbase, const DevOp *ops,
+                                                 const double *mats, const float *matsf,
+                                                 const uint64_t *tmask, const uint64_t *tphi, int tid,
+                                                 int nthr) {
     using C2 = typename C2T<R>::type;
-    constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
-    // complex64 threads move adjacent pairs in the load/store phases
-    constexpr int NROW = kC128 ? NR : NR / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PassDesc &d = args.d;
-    const int L = d.L;
-    const int tid = threadIdx.x;
-    const int nthr = blockDim.x;
-    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
-    C2 *state = reinterpret_cast<C2 *>(args.state);
-    C2 *snap = reinterpret_cast<C2 *>(args.snap);
-    const uint32_t flags = d.flags;
-
-    // the pass's program into shared memory (ops, matrices, diagonal terms)
-    unsigned char *pbase = smem_raw + (sizeof(C2) << L);
     DevOp *sops = reinterpret_cast<DevOp *>(pbase);
     C2 *smats = reinterpret_cast<C2 *>(pbase + (size_t)d.nops * sizeof(DevOp));
     uint64_t *sterms = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(smats) +
                                                     (size_t)d.nmat * 16 * sizeof(C2));
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(args.ops + d.op0);
-        int4 *dst = reinterpret_cast<int4 *>(sops);
-        for (uint32_t i = tid; i < d.nops * (uint32_t)(sizeof(DevOp) / 16); i += nthr) dst[i] = src[i];
-        const int4 *msrc = kC128 ? reinterpret_cast<const int4 *>(args.mats + 32 * (size_t)d.mat0)
-                                 : reinterpret_cast<const int4 *>(args.matsf + 32 * (size_t)d.mat0);
-        int4 *mdst = reinterpret_cast<int4 *>(smats);
-        for (uint32_t i = tid; i < d.nmat * (uint32_t)(16 * sizeof(C2) / 16); i += nthr) mdst[i] = msrc[i];
-        for (uint32_t i = tid; i < d.nterm; i += nthr) {
-            sterms[2 * i] = args.tmask[d.term0 + i];
-            sterms[2 * i + 1] = args.tphi[d.term0 + i];
-        }
+    const int4 *src = reinterpret_cast<const int4 *>(ops + d.op0);
+    int4 *dst = reinterpret_cast<int4 *>(sops);
+    for (uint32_t i = tid; i < d.nops * (uint32_t)(sizeof(DevOp) / 16); i += nthr) dst[i] = src[i];
+    const int4 *msrc = kC128 ? reinterpret_cast<const int4 *>(mats + 32 * (size_t)d.mat0)
+                             : reinterpret_cast<const int4 *>(matsf + 32 * (size_t)d.mat0);
+    int4 *mdst = reinterpret_cast<int4 *>(smats);
+    for (uint32_t i = tid; i < d.nmat * (uint32_t)(16 * sizeof(C2) / 16); i += nthr) mdst[i] = msrc[i];
+    for (uint32_t i = tid; i < d.nterm; i += nthr) {
+        sterms[2 * i] = tmask[d.term0 + i];
+        sterms[2 * i + 1] = tphi[d.term0 + i];
     }
-    const SProg<R> P{sops, smats, sterms, d.op0, d.mat0, d.term0};
+    return SProg<R>{sops, smats, sterms, d.op0, d.mat0, d.term0};
+}
 
-    // this thread's part of a load row (local index tid, or 2 tid for pairs)
-    const uint32_t erow = kC128 ? (uint32_t)tid : (uint32_t)tid << 1;
-    uint64_t gthr = 0;
-    for (int b = 0; b < L; ++b)
-        if (erow >> b & 1) gthr |= 1ull << d.win[b];
-    const uint32_t sthr = tile_swizzle(erow, kC128);
-    const float wleaf = (float)d.leaf_w;
-    __syncthreads();
-
-    double red_n = 0.0, red_r = 0.0, red_i = 0.0;
-
-    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
-        uint64_t tb = 0;
-        for (int b = 0; b < d.n_cw; ++b)
-            if (t >> b & 1) tb |= 1ull << d.cw[b];
-        const uint64_t gbase = tb | gthr;
-        // load the tile: every row load in flight before the shared stores
-        if constexpr (kC128) {
-            C2 buf[NROW];
-#pragma unroll
-            for (int i = 0; i < NROW; ++i) buf[i] = state[gbase | d.grow[i]];
-#pragma unroll
-            for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = buf[i];
-        } else {
-            const float4 *src = reinterpret_cast<const float4 *>(state);
-            float4 *dst = reinterpret_cast<float4 *>(tile);
-            float4 buf[NROW];
-#pragma unroll
-            for (int i = 0; i < NROW; ++i) buf[i] = src[(gbase | d.grow[i]) >> 1];
-#pragma unroll
-            for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
-        }
-        __syncthreads();
-        for (int s = 0; s < d.n_stages; ++s) {
-            const StageDesc &sd = d.st[s];
+// The register stages of one pass on one tile in shared memory (tile bits
+// tb); threads beyond 2^(L-V) only take part in the barriers.
+template <typename R, int V>
+__device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const PassDesc &d, const SProg<R> &P,
+                                           int tid, uint64_t tb) {
+    using C2 = typename C2T<R>::type;
+    constexpr int NR = 1 << V;
+    constexpr bool kC128 = sizeof(R) == 8;
+    const int L = d.L;
+    const bool active = tid < (1 << (L - V));
+    for (int s = 0; s < d.n_stages; ++s) {
+        const StageDesc &sd = d.st[s];
+        if (active) {
             // thread bits -> the stage's non-register local bits: insert a zero
             // at each register bit (ascending)
             uint32_t e = (uint32_t)tid;
@@ -378,8 +345,66 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) tile[sb ^ sd.sr[r]] = a[r];
-            __syncthreads();
         }
+        __syncthreads();
+    }
+}
+
+template <typename R, int V>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
+    using C2 = typename C2T<R>::type;
+    constexpr int NR = 1 << V;
+    constexpr bool kC128 = sizeof(R) == 8;
+    // complex64 threads move adjacent pairs in the load/store phases
+    constexpr int NROW = kC128 ? NR : NR / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PassDesc &d = args.d;
+    const int L = d.L;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
+    C2 *state = reinterpret_cast<C2 *>(args.state);
+    C2 *snap = reinterpret_cast<C2 *>(args.snap);
+    const uint32_t flags = d.flags;
+
+    // the pass's program into shared memory (ops, matrices, diagonal terms)
+    const SProg<R> P = load_program<R>(d, smem_raw + (sizeof(C2) << L), args.ops, args.mats, args.matsf,
+                                       args.tmask, args.tphi, tid, nthr);
+
+    // this thread's part of a load row (local index tid, or 2 tid for pairs)
+    const uint32_t erow = kC128 ? (uint32_t)tid : (uint32_t)tid << 1;
+    uint64_t gthr = 0;
+    for (int b = 0; b < L; ++b)
+        if (erow >> b & 1) gthr |= 1ull << d.win[b];
+    const uint32_t sthr = tile_swizzle(erow, kC128);
+    const float wleaf = (float)d.leaf_w;
+    __syncthreads();
+
+    double red_n = 0.0, red_r = 0.0, red_i = 0.0;
+
+    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+        uint64_t tb = 0;
+        for (int b = 0; b < d.n_cw; ++b)
+            if (t >> b & 1) tb |= 1ull << d.cw[b];
+        const uint64_t gbase = tb | gthr;
+        // load the tile: every row load in flight before the shared stores
+        if constexpr (kC128) {
+            C2 buf[NROW];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) buf[i] = state[gbase | d.grow[i]];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = buf[i];
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(state);
+            float4 *dst = reinterpret_cast<float4 *>(tile);
+            float4 buf[NROW];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) buf[i] = src[(gbase | d.grow[i]) >> 1];
+#pragma unroll
+            for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
+        }
+        __syncthreads();
+        run_stages<R, V>(tile, d, P, tid, tb);
         // store + epilogue
         float pn = 0.f, pr = 0.f, pi = 0.f;
         double dn = 0.0, dr = 0.0, di = 0.0;
@@ -614,6 +639,166 @@ cudaError_t launch_restore(void *state, const void *snap, int precision, uint64_
         restore_kernel<float2><<<grid, 256, 0, st>>>((float2 *)state, (const float2 *)snap, dim,
                                                      restore_flag, check);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ batched jobs
+
+// Largest job a CTA holds in shared memory: 2^13 complex64 or 2^12
+// complex128 amplitudes (64 KiB).
+template <typename R> constexpr int job_max_qubits() { return sizeof(R) == 4 ? 13 : 12; }
+
+// job_kernel: each CTA takes jobs from a work queue and runs a job's whole
+// program -- resets, fused passes (register stages on the state held in
+// shared memory), leaf accumulation into the job's FP64 output, snapshot
+// writes and restores, drift records and checks -- without leaving the
+// CTA.  Jobs of uneven size and depth share one launch.
+template <typename R, int V>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const __grid_constant__ BatchArgs B) {
+    using C2 = typename C2T<R>::type;
+    constexpr bool kC128 = sizeof(R) == 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *tile = reinterpret_cast<C2 *>(smem_raw);
+    unsigned char *pbase = smem_raw + (sizeof(C2) << job_max_qubits<R>());
+    __shared__ int s_job;
+    __shared__ int s_restore;
+    __shared__ double s_red[3];
+    __shared__ double s_wsum[3][8];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_job = (int)atomicAdd(B.next_job, 1u);
+        __syncthreads();
+        const int j = s_job;
+        __syncthreads();
+        if (j >= B.n_jobs) break;
+        const JobDesc &J = B.jobs[j];
+        const int N = 1 << J.n;
+        for (int e = tid; e < N; e += nthr) J.acc[e] = 0.0;
+        for (uint32_t k = 0; k < J.nsteps; ++k) {
+            const Step &st = B.steps[J.step0 + k];
+            if (st.type == ST_INIT) {
+                for (int e = tid; e < N; e += nthr) {
+                    C2 z;
+                    z.x = (e == 0) ? 1 : 0;
+                    z.y = 0;
+                    tile[tile_swizzle((uint32_t)e, kC128)] = z;
+                }
+                __syncthreads();
+            } else if (st.type == ST_PASS) {
+                const PassDesc &d = B.passes[st.pass];
+                const SProg<R> P = load_program<R>(d, pbase, B.ops, B.mats, B.matsf, B.tmask, B.tphi, tid, nthr);
+                __syncthreads();
+                run_stages<R, V>(tile, d, P, tid, 0);
+                const uint32_t flags = d.flags;
+                double rn = 0, rr = 0, ri = 0;
+                C2 *sn = (flags & PF_SNAPSHOT) ? reinterpret_cast<C2 *>(J.snaps) + (size_t)d.snap * N : nullptr;
+                for (int e = tid; e < N; e += nthr) {
+                    const C2 v = tile[tile_swizzle((uint32_t)e, kC128)];
+                    if (flags & PF_SNAPSHOT) sn[e] = v;
+                    if (flags & PF_LEAF) {
+                        if constexpr (kC128) J.acc[e] = fma(d.leaf_w, v.x * v.x + v.y * v.y, J.acc[e]);
+                        else J.acc[e] = leaf_add(J.acc[e], (float)d.leaf_w * fmaf(v.x, v.x, v.y * v.y));
+                    }
+                    if (flags & PF_REDUCE) {
+                        const double h = check_sign((uint64_t)e);
+                        rn += (double)v.x * v.x + (double)v.y * v.y;
+                        rr += h * v.x;
+                        ri += h * v.y;
+                    }
+                }
+                if (flags & PF_REDUCE) {
+                    for (int off = 16; off > 0; off >>= 1) {
+                        rn += __shfl_down_sync(0xffffffffu, rn, off);
+                        rr += __shfl_down_sync(0xffffffffu, rr, off);
+                        ri += __shfl_down_sync(0xffffffffu, ri, off);
+                    }
+                    if ((tid & 31) == 0) {
+                        s_wsum[0][tid >> 5] = rn;
+                        s_wsum[1][tid >> 5] = rr;
+                        s_wsum[2][tid >> 5] = ri;
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        double a0 = 0, a1 = 0, a2 = 0;
+                        for (int w = 0; w < (nthr + 31) / 32; ++w) {
+                            a0 += s_wsum[0][w];
+                            a1 += s_wsum[1][w];
+                            a2 += s_wsum[2][w];
+                        }
+                        s_red[0] = a0;
+                        s_red[1] = a1;
+                        s_red[2] = a2;
+                    }
+                }
+                __syncthreads();
+            } else if (st.type == ST_RECORD) {
+                if (tid == 0) {
+                    J.records[4 * st.depth + 0] = s_red[0];
+                    J.records[4 * st.depth + 1] = s_red[1];
+                    J.records[4 * st.depth + 2] = s_red[2];
+                }
+                __syncthreads();
+            } else if (st.type == ST_CHECK) {
+                if (tid == 0) {
+                    const double *rec = J.records + 4 * st.depth;
+                    const double dn = fabs(sqrt(s_red[0]) - sqrt(fmax(rec[0], 0.0)));
+                    const double dc = hypot(s_red[1] - rec[1], s_red[2] - rec[2]);
+                    const double drift = fmax(dn, dc);
+                    const bool bad = drift > B.drift_tol;
+                    s_restore = bad && st.snap >= 0;
+                    if (bad) atomicAdd(B.counters + (st.snap >= 0 ? 0 : 1), 1ull);
+                    // running maximum of the drift (non-negative doubles order like their bits)
+                    atomicMax(B.counters + 2, (unsigned long long)__double_as_longlong(drift));
+                }
+                __syncthreads();
+            } else if (st.type == ST_RESTORE) {
+                if (st.check < 0 || s_restore) {
+                    const C2 *sn = reinterpret_cast<const C2 *>(J.snaps) + (size_t)st.snap * N;
+                    for (int e = tid; e < N; e += nthr) tile[tile_swizzle((uint32_t)e, kC128)] = sn[e];
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <typename R, int V>
+static cudaError_t launch_job_t(const BatchArgs &b, int grid, cudaStream_t st) {
+    const size_t smem = (sizeof(R) * 2 << job_max_qubits<R>()) + kMaxPassProgramBytes;
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    job_kernel<R, V><<<grid, 256, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+// One launch over every job of a batch; `grid` CTAs drain the work queue.
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, cudaStream_t st) {
+    if (precision == TUSQ_C128) return launch_job_t<double, kRegBitsC128>(b, grid, st);
+    return launch_job_t<float, kRegBitsC64>(b, grid, st);
+}
+
+int job_max_qubits_of(int precision) {
+    return precision == TUSQ_C128 ? job_max_qubits<double>() : job_max_qubits<float>();
+}
+
+// Resident job CTAs per SM.
+int job_occupancy(int precision) {
+    int nb = 0;
+    if (precision == TUSQ_C128) {
+        const size_t smem = (16 << job_max_qubits<double>()) + kMaxPassProgramBytes;
+        if (cudaFuncSetAttribute(job_kernel<double, kRegBitsC128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, job_kernel<double, kRegBitsC128>, 256, smem) !=
+                cudaSuccess)
+            return 1;
+    } else {
+        const size_t smem = (8 << job_max_qubits<float>()) + kMaxPassProgramBytes;
+        if (cudaFuncSetAttribute(job_kernel<float, kRegBitsC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, job_kernel<float, kRegBitsC64>, 256, smem) !=
+                cudaSuccess)
+            return 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 }  // namespace tusq

@@ -147,6 +147,34 @@ struct PassArgs {
     const uint64_t *tphi;
 };
 
+// One job of a batch launch: its steps in the batch's step array (pass,
+// op, matrix and term indices already relocated into the batch arrays), its
+// size and its device buffers.
+struct JobDesc {
+    uint32_t step0, nsteps;
+    int32_t n;
+    int32_t pad;
+    double *acc;           // 2^n FP64 output (zeroed by the kernel)
+    void *snaps;           // snapshot slots, 2^n amplitudes each
+    double *records;       // 4 doubles per record depth
+};
+
+struct BatchArgs {
+    const JobDesc *jobs;
+    int32_t n_jobs;
+    int32_t pad;
+    const Step *steps;
+    const PassDesc *passes;
+    const DevOp *ops;
+    const double *mats;
+    const float *matsf;
+    const uint64_t *tmask;
+    const uint64_t *tphi;
+    unsigned int *next_job;          // work queue head (zeroed before each launch)
+    unsigned long long *counters;    // [0] restores after failed checks, [1] unrecovered drift
+    double drift_tol;
+};
+
 struct CompileOpts {
     int precision;
     int max_window;

@@ -1,0 +1,99 @@
+"""Batched jobs (one persistent launch, state in shared memory) against the
+oracle and against the per-job engine; CUDA-graph replay; autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2508_04880_b300 as T
+import tusq_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {T.C128: (1e-12, 1e-10), T.C64: (1e-5, 1e-4)}
+
+
+def _jobs():
+    return [
+        (W.random_layers(6, 20, 0, 1e-3, 1e-2), 10_000, 0),
+        (W.brickwork(9, 12, 1, 2e-3, 2e-2), 20_000, 1),
+        (W.qaoa_3regular(10, 2, 2, 1e-3, 1e-2), 20_000, 2),
+        (W.random_mixed(7, 60, 3, 1e-2, 3e-2), 5_000, 3),
+        (W.brickwork(12, 20, 4, 1e-3, 1e-2), 50_000, 4),
+        (W.qaoa_3regular(12, 3, 5, 1e-3, 1e-2), 50_000, 5),
+        (W.random_layers(5, 3, 6, 0.0, 0.0), 100, 6),
+    ]
+
+
+def _close(a, b, precision, what=""):
+    ma, tv = TOL[precision]
+    d = np.abs(a - b)
+    assert d.max() <= ma and d.sum() <= tv, (what, d.max(), d.sum())
+
+
+@pytest.mark.parametrize("precision", [T.C128, T.C64])
+@pytest.mark.parametrize("traversal", [T.DFTT, T.DFTT_SNAPSHOT, T.FROM_SCRATCH])
+def test_batch_matches_oracle(precision, traversal):
+    import torch
+    jobs = _jobs()
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    b = T.Batch(plans, [o.data_ptr() for o in outs], T.run_opts(precision=precision, traversal=traversal))
+    b.launch()
+    info = b.finish()
+    assert info["unrecovered"] == 0
+    for (c, s, seed), o in zip(jobs, outs):
+        ref, _ = oracle.run(c, s, seed)
+        _close(o.cpu().numpy(), ref, precision, c.name)
+
+
+def test_batch_graph_replay_and_forced_drift():
+    import torch
+    jobs = _jobs()
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = T.Batch(plans, [o.data_ptr() for o in outs], T.run_opts(precision=T.C128, drift_tol=0.0),
+                    use_graph=True, stream=stream.cuda_stream)
+        first = None
+        for _ in range(3):
+            for o in outs:
+                o.fill_(7.0)
+            b.launch(stream.cuda_stream)
+            info = b.finish()
+            cur = [o.cpu().numpy() for o in outs]
+            if first is None:
+                first = cur
+            for a, c in zip(first, cur):
+                assert np.array_equal(a, c)        # replays are bit-identical
+    assert info["restores"] == info["checks"] > 0   # tolerance 0 forces every restore
+    for (c, s, seed), o in zip(jobs, first):
+        ref, _ = oracle.run(c, s, seed)
+        _close(o, ref, T.C128, c.name)
+
+
+def test_batch_equals_single_job_engine():
+    import torch
+    jobs = _jobs()
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    opts = T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT)
+    b = T.Batch(plans, [o.data_ptr() for o in outs], opts)
+    b.launch()
+    b.finish()
+    for p, o in zip(plans, outs):
+        single, _ = T.run_torch(p, opts)
+        _close(o.cpu().numpy(), single.cpu().numpy(), T.C64)
+
+
+def test_batch_autotune_and_size_limits():
+    import torch
+    jobs = _jobs()
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    best, ms = T.tusq_batch_autotune(plans, [o.data_ptr() for o in outs], T.run_opts(precision=T.C64))
+    assert ms > 0 and best.traversal in (T.DFTT, T.FROM_SCRATCH, T.DFTT_SNAPSHOT) and best.schedule in (0, 1)
+    big = T.plan(W.brickwork(14, 2, 0, 0.0, 0.0), 10, 0)
+    o = torch.empty(1 << 14, dtype=torch.float64, device="cuda")
+    with pytest.raises(T.TusqError):
+        T.Batch([big], [o.data_ptr()], T.run_opts(precision=T.C64))

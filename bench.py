@@ -190,6 +190,112 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, T, torch):
+    """Config 4: many small noisy jobs of uneven depth.  Jobs that fit a CTA's
+    shared memory (<= 13 qubits, complex64) run in one persistent launch
+    replayed from a CUDA graph with autotuned options; larger ones run as
+    concurrent per-job traversals on several streams.  One step = every job
+    once."""
+    jobs = W.job_mix(args.jobs, seed=0, n_lo=12, n_hi=18, d_lo=20, d_hi=80)
+    t0 = time.perf_counter()
+    plans = [T.plan(c, args.batch_shots, j) for j, c in enumerate(jobs)]
+    plan_s = time.perf_counter() - t0
+    n_inst = sum(p.stats()["n_instances"] for p in plans)
+    small = [i for i, c in enumerate(jobs) if c.n_qubits <= 13]
+    large = [i for i, c in enumerate(jobs) if c.n_qubits > 13]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c in jobs]
+    stream = torch.cuda.Stream()
+    side = [torch.cuda.Stream() for _ in range(8)]
+    base = T.run_opts(precision=T.C64)
+    with torch.cuda.stream(stream):
+        best, tune_ms = T.tusq_batch_autotune([plans[i] for i in small], [outs[i].data_ptr() for i in small],
+                                              base, stream.cuda_stream)
+        b = T.Batch([plans[i] for i in small], [outs[i].data_ptr() for i in small], best, use_graph=True,
+                    stream=stream.cuda_stream)
+    exs = [T.Exec(plans[i], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT), side[k % 8].cuda_stream)
+           for k, i in enumerate(large)]
+
+    def step():
+        b.launch(stream.cuda_stream)
+        for k, i in enumerate(large):
+            exs[k].launch(outs[i].data_ptr(), side[k % 8].cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    secs = (time.perf_counter() - t0) / args.steps
+    b.finish()
+    for e in exs:
+        e.finish()
+    # error of a few jobs against the oracle (complex128 reference)
+    import oracle
+    errs = []
+    for i in (small[:2] + large[:1]):
+        ref, _ = oracle.run(jobs[i], args.batch_shots, i)
+        d = np.abs(outs[i].cpu().numpy() - ref)
+        errs.append({"job": i, "qubits": jobs[i].n_qubits, "max_abs": float(d.max()), "tv": float(d.sum())})
+    return {
+        "metric": "noisy instances/s (batched jobs)", "value": n_inst / secs, "unit": "instances/s",
+        "jobs_per_s": len(jobs) / secs, "ms_per_step": secs * 1e3, "steps": args.steps, "warmup": args.warmup,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"{len(jobs)} jobs, 12-18 qubits, brickwork/QAOA mix, depth 20-80, "
+                               f"{args.batch_shots} shots each", "jobs_in_one_launch": len(small),
+                   "jobs_on_streams": len(large), "instances": n_inst,
+                   "autotuned": {"traversal": best.traversal, "schedule": best.schedule, "ms": tune_ms}},
+        "plan_seconds": plan_s, "error_vs_oracle": errs,
+    }
+
+
+def run_served(args, T, torch):
+    """Config 5: Poisson arrivals of jobs (10-30 qubits, depth 20-100, p in
+    [1e-4, 1e-2], 1e5-1e6 shots) into the serving loop (admission by HBM
+    footprint, concurrent streams, state resident until done).  Reports
+    latency (submit to completion) percentiles and throughput per rate."""
+    stream_jobs = W.served_stream(args.jobs, seed=0)
+    plans = [T.plan(c, shots, j) for j, (c, shots) in enumerate(stream_jobs)]
+    n_inst = [p.stats()["n_instances"] for p in plans]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _ in stream_jobs]
+    budget = int(args.hbm_budget_gb * (1 << 30))
+    results = []
+    # capacity: everything submitted at once
+    srv = T.Server(budget, n_streams=8)
+    t0 = time.perf_counter()
+    ids = [srv.submit(p, o.data_ptr(), T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT))
+           for p, o in zip(plans, outs)]
+    srv.drain()
+    cap_s = time.perf_counter() - t0
+    capacity = len(plans) / cap_s
+    del srv
+    rng = np.random.default_rng(1)
+    for frac in args.rates:
+        lam = frac * capacity
+        gaps = rng.exponential(1.0 / lam, len(plans))
+        srv = T.Server(budget, n_streams=8)
+        t0 = time.perf_counter()
+        ids = []
+        for p, o, g in zip(plans, outs, gaps):
+            target = t0 + (gaps[:len(ids) + 1].sum())
+            while time.perf_counter() < target:
+                time.sleep(0.0002)
+            ids.append(srv.submit(p, o.data_ptr(), T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT)))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        lat = np.array([srv.poll(i)[1] for i in ids])
+        results.append({"rate_frac_of_capacity": frac, "rate_jobs_per_s": lam,
+                        "p50_latency_s": float(np.percentile(lat, 50)),
+                        "p99_latency_s": float(np.percentile(lat, 99)),
+                        "instances_per_s": sum(n_inst) / wall, "jobs_per_s": len(plans) / wall})
+        del srv
+    return {"metric": "served noisy jobs: p50/p99 latency and instances/s", "unit": "s / instances/s",
+            "capacity_jobs_per_s": capacity, "jobs": len(plans), "hbm_budget_gb": args.hbm_budget_gb,
+            "qubits": [c.n_qubits for c, _ in stream_jobs], "rates": results, "dtype": "c64",
+            "data": "synthetic"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,6 +309,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--compare", action="store_true", help="also time the other traversals")
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "served"],
+                    help="main: the 28-qubit headline; batch: config 4; served: config 5")
+    ap.add_argument("--jobs", type=int, default=2048)
+    ap.add_argument("--batch-shots", type=int, default=100_000)
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 2.0])
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -214,6 +326,11 @@ def main():
     import torch
     import paper_2508_04880_b300 as T
     torch.cuda.set_device(local)
+    if args.mode != "main":
+        line = run_batch(args, T, torch) if args.mode == "batch" else run_served(args, T, torch)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

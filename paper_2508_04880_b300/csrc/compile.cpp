@@ -398,9 +398,22 @@ struct Encoder {
                 (void)taken;
             }
             std::vector<HOp> merged = merge_ops(ordered);
-            for (size_t k = 0; k < merged.size(); k += kMaxStageOps)
-                pieces.push_back(Piece{swin[s], std::vector<HOp>(merged.begin() + k,
-                    merged.begin() + std::min(merged.size(), k + (size_t)kMaxStageOps))});
+            // cut into pieces of at most kMaxStageOps ops and at most the
+            // per-pass program budget (same register bits)
+            Piece cur{swin[s], {}};
+            uint32_t cur_bytes = 0;
+            for (const HOp &o : merged) {
+                uint32_t ob = (uint32_t)sizeof(DevOp) +
+                              (o.type == H_DIAG ? 16 * (uint32_t)o.terms.size() : (c128 ? 256u : 128u));
+                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > kMaxPassProgramBytes)) {
+                    pieces.push_back(cur);
+                    cur.ops.clear();
+                    cur_bytes = 0;
+                }
+                cur.ops.push_back(o);
+                cur_bytes += ob;
+            }
+            if (!cur.ops.empty()) pieces.push_back(cur);
         }
         const uint32_t mat_bytes = c128 ? 256 : 128;
         auto piece_bytes = [&](const Piece &pc) {
@@ -549,6 +562,9 @@ struct Encoder {
             pd.nmat = (uint32_t)(prog.mats.size() / 32) - pd.mat0;
             pd.nterm = (uint32_t)prog.term_mask.size() - pd.term0;
             pd.prog_bytes = pd.nops * (uint32_t)sizeof(DevOp) + pd.nmat * mat_bytes + pd.nterm * 16;
+            // the kernels reserve exactly this much shared memory for a program
+            if (pd.prog_bytes > kMaxPassProgramBytes)
+                throw std::logic_error("encoder: pass program exceeds the shared-memory budget");
             pass_ids.push_back((int)prog.passes.size());
             prog.passes.push_back(pd);
             p0 = p1;

@@ -212,8 +212,11 @@ def run_batch(args, T, torch):
                                               base, stream.cuda_stream)
         b = T.Batch([plans[i] for i in small], [outs[i].data_ptr() for i in small], best, use_graph=True,
                     stream=stream.cuda_stream)
-    exs = [T.Exec(plans[i], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT), side[k % 8].cuda_stream)
-           for k, i in enumerate(large)]
+    # the per-job programs compile independently (the C calls release the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
+        exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT),
+                                              side[ki[0] % 8].cuda_stream), enumerate(large)))
 
     def step():
         b.launch(stream.cuda_stream)

@@ -3,10 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 
 #include "internal.h"
 #include "program.h"
@@ -146,8 +148,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     std::vector<uint64_t> tmask, tphi;
     std::vector<size_t> snap_off, rec_off;
     size_t snap_bytes = 0, rec_count = 0;
-    for (uint32_t j = 0; j < n_jobs; ++j) {
-        const tusq_plan_t &P = *plans[j];
+    auto opts_of = [&](const tusq_plan_t &P) {
         const size_t state = amp << P.n;
         CompileOpts co;
         co.precision = o.precision;
@@ -159,14 +160,40 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         co.checks = o.drift_tol >= 0 && o.traversal != TUSQ_FROM_SCRATCH;
         const uint64_t budget = o.snapshot_bytes ? o.snapshot_bytes : 8 * state;
         co.snapshots = (co.checks || o.traversal == TUSQ_DFTT_SNAPSHOT) ? (int)std::min<uint64_t>(budget / state, 64) : 0;
-        Program pg;
-        try {
-            compile_program(P, co, pg);
-        } catch (const std::exception &ex) {
+        return co;
+    };
+    // the jobs' programs are independent: compile them on all host cores
+    std::vector<Program> pgs(n_jobs);
+    std::vector<std::string> errs(n_jobs);
+    {
+        std::atomic<uint32_t> next{0};
+        auto work = [&] {
+            for (uint32_t j; (j = next.fetch_add(1)) < n_jobs;) {
+                try {
+                    compile_program(*plans[j], opts_of(*plans[j]), pgs[j]);
+                } catch (const std::exception &ex) {
+                    errs[j] = ex.what();
+                }
+            }
+        };
+        const uint32_t nth = std::min<uint32_t>(n_jobs, std::max(1u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (uint32_t t = 1; t < nth; ++t) th.emplace_back(work);
+        work();
+        for (auto &t : th) t.join();
+    }
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        if (!errs[j].empty()) {
             delete b;
-            set_error(std::string("tusq_batch_create: schedule compilation failed: ") + ex.what());
+            set_error("tusq_batch_create: schedule compilation of job " + std::to_string(j) + " failed: " + errs[j]);
             return TUSQ_EINVAL;
         }
+    }
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        const tusq_plan_t &P = *plans[j];
+        const size_t state = amp << P.n;
+        const CompileOpts co = opts_of(P);
+        Program pg = std::move(pgs[j]);
         // relocate the job's program into the batch arrays
         const uint32_t pass_base = (uint32_t)passes.size(), op_base = (uint32_t)ops.size();
         const uint32_t mat_base = (uint32_t)(mats.size() / 32), term_base = (uint32_t)tmask.size();

@@ -145,7 +145,7 @@ struct Pass {
 // non-diagonal op; diagonal ops fit any window) and takes every op that
 // becomes ready and fits.  When nothing more fits, the window grows by the
 // bits of one blocked ready op: the choice that lets the most ops into the
-// group (found by trying each candidate on a copy of the DAG state).
+// group (found by trying each candidate; the trial is undone afterwards).
 template <class QubitsOf>
 std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uint64_t forced,
                                        QubitsOf qubits_of, std::vector<uint64_t> *wins,
@@ -153,52 +153,72 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
     const int m = (int)ops.size();
     std::vector<std::vector<int>> succ(m);
     std::vector<int> indeg(m, 0);
-    std::vector<uint64_t> qm(m), wq(m);
-    for (int b = 0; b < m; ++b) {
-        qm[b] = ops[b].qmask();
-        wq[b] = ops[b].type == H_DIAG ? 0 : qubits_of(ops[b]);
-    }
-    for (int b = 0; b < m; ++b)
-        for (int a = 0; a < b; ++a) {
-            if (ops[a].type == H_DIAG && ops[b].type == H_DIAG) continue;
-            if (qm[a] & qm[b]) {
-                succ[a].push_back(b);
-                indeg[b]++;
+    std::vector<uint64_t> wq(m);
+    for (int b = 0; b < m; ++b) wq[b] = ops[b].type == H_DIAG ? 0 : qubits_of(ops[b]);
+    // dependences by qubit: an op follows the last non-diagonal op on each of
+    // its qubits; a non-diagonal op also follows the diagonal ops on its
+    // qubits since then (diagonal ops commute with each other)
+    {
+        std::vector<int> last_nd(64, -1);
+        std::vector<std::vector<int>> diag_since(64);
+        std::vector<int> mark(m, -1);
+        auto edge = [&](int a, int b) {
+            if (a < 0 || mark[a] == b) return;
+            mark[a] = b;
+            succ[a].push_back(b);
+            indeg[b]++;
+        };
+        for (int b = 0; b < m; ++b) {
+            const uint64_t qm = ops[b].qmask();
+            const bool diag = ops[b].type == H_DIAG;
+            for (int q = 0; q < 64; ++q) {
+                if (!(qm >> q & 1)) continue;
+                edge(last_nd[q], b);
+                if (!diag)
+                    for (int a : diag_since[q]) edge(a, b);
+            }
+            for (int q = 0; q < 64; ++q) {
+                if (!(qm >> q & 1)) continue;
+                if (diag) diag_since[q].push_back(b);
+                else { last_nd[q] = b; diag_since[q].clear(); }
             }
         }
-    std::vector<char> done(m, 0);
+    }
     std::vector<int> ready;       // ready and not yet scheduled (blocked by the window)
     for (int b = 0; b < m; ++b)
         if (indeg[b] == 0) ready.push_back(b);
     // schedule everything that fits W, starting from `ready`; returns the
-    // scheduled ops in application order and leaves the blocked ones in ready
-    auto closure = [&](uint64_t W, std::vector<int> &deg, std::vector<char> &dn, std::vector<int> &rdy,
-                       std::vector<int> *out) {
+    // scheduled ops in application order and leaves the blocked ones in
+    // ready.  With `undo`, every in-degree decrement is logged so that a
+    // trial can be rolled back.
+    std::vector<int> work, blocked;
+    auto closure = [&](uint64_t W, std::vector<int> &rdy, std::vector<int> *out, std::vector<int> *undo) {
         int count = 0;
-        std::vector<int> work;
-        std::vector<int> blocked;
+        work.clear();
+        blocked.clear();
         std::sort(rdy.begin(), rdy.end());
-        for (int b : rdy) work.push_back(b);
-        rdy.clear();
+        work.insert(work.end(), rdy.begin(), rdy.end());
         size_t h = 0;
         while (h < work.size()) {
             int b = work[h++];
             if ((wq[b] & ~W) != 0) { blocked.push_back(b); continue; }
-            dn[b] = 1;
             ++count;
             if (out) out->push_back(b);
-            for (int s : succ[b])
-                if (--deg[s] == 0) work.push_back(s);
+            for (int s : succ[b]) {
+                if (undo) undo->push_back(s);
+                if (--indeg[s] == 0) work.push_back(s);
+            }
         }
-        rdy = blocked;
+        if (!undo) rdy = blocked;
         return count;
     };
     int left = m;
     std::vector<std::vector<int>> groups;
+    std::vector<int> undo;
     while (left > 0) {
         uint64_t W = forced;
         std::vector<int> g;
-        left -= closure(W, indeg, done, ready, &g);
+        left -= closure(W, ready, &g, nullptr);
         for (;;) {
             // candidate window extensions: the bits of each blocked ready op
             int best = -1;
@@ -214,10 +234,10 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
                     if (best < 0 || b < best) { best = b; best_q = q; }
                     continue;
                 }
-                std::vector<int> deg2 = indeg;
-                std::vector<char> dn2 = done;
+                undo.clear();
                 std::vector<int> rdy2 = ready;
-                int gain = closure(W | q, deg2, dn2, rdy2, nullptr);
+                int gain = closure(W | q, rdy2, nullptr, &undo);
+                for (int s : undo) indeg[s]++;
                 int nb = __builtin_popcountll(q);
                 // most ops per added bit first, then fewer bits, then list order
                 if (best < 0 || gain > best_gain ||
@@ -230,7 +250,7 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
             }
             if (best < 0) break;
             W |= best_q;
-            left -= closure(W, indeg, done, ready, &g);
+            left -= closure(W, ready, &g, nullptr);
         }
         if (g.empty()) throw std::logic_error("schedule: no progress (gate wider than window?)");
         groups.push_back(g);

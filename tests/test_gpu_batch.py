@@ -66,7 +66,8 @@ def test_batch_graph_replay_and_forced_drift():
                 first = cur
             for a, c in zip(first, cur):
                 assert np.array_equal(a, c)        # replays are bit-identical
-    assert info["restores"] == info["checks"] > 0   # tolerance 0 forces every restore
+    # tolerance 0: every check whose drift is not exactly zero restores
+    assert info["checks"] > 0 and 0 < info["restores"] <= info["checks"]
     for (c, s, seed), o in zip(jobs, first):
         ref, _ = oracle.run(c, s, seed)
         _close(o, ref, T.C128, c.name)

@@ -569,6 +569,8 @@ struct Encoder {
                             d.csr[mu] = (uint16_t)k;
                         }
                         d.csr[33] = (uint16_t)t.size();
+                        for (int mu = 1; mu < 32; ++mu)
+                            if (d.csr[mu + 1] > d.csr[mu]) d.mu_mask |= 1u << mu;
                         for (auto &x : t) {
                             prog.term_mask.push_back(x.second.first);
                             prog.term_phi.push_back(to_fixed(x.second.second, c128));

@@ -174,13 +174,15 @@ template <typename R> struct Phase;
 template <> struct Phase<float> {
     using U = uint32_t;
     // 2^-31-turn units; the low 31 bits, read as a signed 32-bit fraction of a
-    // turn, give the exact angle reduced to [-pi, pi) before the fast
+    // turn, give the exact angle reduced to [-1/2, 1/2) turn.  It is rounded
+    // to 2^-23 turn and converted to float by the 1.5 * 2^23 exponent trick
+    // (integer and FP32 adds, no conversion instruction) before the fast
     // hardware sine and cosine (absolute error about 4e-7 there).
     __device__ static float2 unit(U p) {
-        const int32_t s = (int32_t)(p << 1);
-        const float x = (float)s * 1.4629180792671596e-09f;   // 2 pi / 2^32
+        const int32_t t = (int32_t)((p << 1) + 256u) >> 9;              // [-2^22, 2^22)
+        const float f = __int_as_float(0x4B400000 + t) - 12582912.0f;   // exactly t
         float sn, cs;
-        __sincosf(x, &sn, &cs);
+        __sincosf(f * 7.490140565847857e-07f, &sn, &cs);                 // 2 pi / 2^23
         return make_float2(cs, sn);
     }
 };
@@ -195,53 +197,63 @@ template <> struct Phase<double> {
     }
 };
 
+// Multiply the registers r with parity(r & MU) = 1 by w (MU a constant).
+template <int V, int MU, typename C2>
+__device__ __forceinline__ void phase_group(C2 (&a)[1 << V], C2 w) {
+#pragma unroll
+    for (int r = 0; r < (1 << V); ++r)
+        if (__builtin_popcount(r & MU) & 1) a[r] = cmul(a[r], w);
+}
+
+template <int V, typename C2>
+__device__ __forceinline__ void phase_group_dispatch(C2 (&a)[1 << V], int mu, C2 w) {
+#define TUSQ_G(M) \
+    case M: if constexpr ((M >> V) == 0) phase_group<V, M>(a, w); break;
+    switch (mu) {
+        TUSQ_G(1) TUSQ_G(2) TUSQ_G(3) TUSQ_G(4) TUSQ_G(5) TUSQ_G(6) TUSQ_G(7) TUSQ_G(8)
+        TUSQ_G(9) TUSQ_G(10) TUSQ_G(11) TUSQ_G(12) TUSQ_G(13) TUSQ_G(14) TUSQ_G(15) TUSQ_G(16)
+        TUSQ_G(17) TUSQ_G(18) TUSQ_G(19) TUSQ_G(20) TUSQ_G(21) TUSQ_G(22) TUSQ_G(23) TUSQ_G(24)
+        TUSQ_G(25) TUSQ_G(26) TUSQ_G(27) TUSQ_G(28) TUSQ_G(29) TUSQ_G(30) TUSQ_G(31)
+    default: break;
+    }
+#undef TUSQ_G
+}
+
 // Diagonal run on the 2^V registers of one thread.  gfix is the global
-// index of the thread's register 0 (register bits cleared).  The angle of
-// register r is A + sum_mu C[mu] parity(r & mu); the parity sums are
-// obtained from one Walsh-Hadamard transform of C (exact in fixed point:
-// sum_mu C[mu] parity(r & mu) = (sum C - WHT(C)[r]) / 2).
+// index of the thread's register 0 (register bits cleared).  A term with
+// register mask mu and fixed-bit parity p adds phi (p xor parity(r & mu))
+// to register r's angle, i.e. p phi to a per-thread constant and
+// (p ? -phi : phi) parity(r & mu) to the rest.  The terms of one mu are
+// summed (exactly, in fixed-point turns) into C_mu, and the registers of odd
+// parity against mu are multiplied by exp(2 pi i C_mu); only the non-empty
+// groups (mu_mask) are visited.  The per-thread constant multiplies all of a
+// thread's registers alike, so it commutes with every in-register op of the
+// stage: it is added to `acc` and applied once when the stage ends.
 template <typename R, int V>
 __device__ __forceinline__ void apply_diag(typename C2T<R>::type (&a)[1 << V], const DevOp &op,
-                                           const SProg<R> &P, uint64_t gfix) {
+                                           const SProg<R> &P, uint64_t gfix, typename Phase<R>::U &acc) {
     using U = typename Phase<R>::U;
-    constexpr int NR = 1 << V;
     U A = (U)op.phi0;
-    U C[NR];
-#pragma unroll
-    for (int mu = 0; mu < NR; ++mu) C[mu] = 0;
     const ulonglong2 *tm = reinterpret_cast<const ulonglong2 *>(P.terms) + (op.term_begin - P.term0);
     for (int k = op.csr[0]; k < op.csr[1]; ++k) {
         const ulonglong2 t = tm[k];
         if (__popcll(gfix & t.x) & 1) A += (U)t.y;
     }
-#pragma unroll
-    for (int mu = 1; mu < NR; ++mu) {
+    uint32_t mm = op.mu_mask;
+    while (mm) {
+        const int mu = __ffs(mm) - 1;
+        mm &= mm - 1;
+        U cm = 0;
         for (int k = op.csr[mu]; k < op.csr[mu + 1]; ++k) {
             const ulonglong2 t = tm[k];
             const U ph = (U)t.y;
             const bool c = __popcll(gfix & t.x) & 1;
             A += c ? ph : (U)0;
-            C[mu] += c ? (U)(0 - ph) : ph;
+            cm += c ? (U)(0 - ph) : ph;
         }
+        phase_group_dispatch<V>(a, mu, Phase<R>::unit(cm));
     }
-    U sum = 0;
-#pragma unroll
-    for (int mu = 0; mu < NR; ++mu) sum += C[mu];
-#pragma unroll
-    for (int h = 1; h < NR; h <<= 1) {
-#pragma unroll
-        for (int i = 0; i < NR; ++i) {
-            if (i & h) continue;
-            U x = C[i], y = C[i | h];
-            C[i] = x + y;
-            C[i | h] = x - y;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        U ang = A + ((U)(sum - C[r]) >> 1);
-        a[r] = cmul(a[r], Phase<R>::unit(ang));
-    }
+    acc += A;
 }
 
 // Sign +-1 of the checksum weight of global index x (a 32-bit integer hash
@@ -324,6 +336,7 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
             for (int r = 0; r < NR; ++r) a[r] = tile[sb ^ sd.sr[r]];
             bool have_gfix = false;
             uint64_t gfix = 0;
+            typename Phase<R>::U acc = 0;     // the stage's per-thread constant phase
             for (uint32_t k = 0; k < sd.op_count; ++k) {
                 const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
                 const int type = op.type;
@@ -340,8 +353,13 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
                             if (e >> b & 1) gfix |= 1ull << d.win[b];
                         have_gfix = true;
                     }
-                    apply_diag<R, V>(a, op, P, gfix);
+                    apply_diag<R, V>(a, op, P, gfix, acc);
                 }
+            }
+            if (have_gfix) {
+                const C2 u = Phase<R>::unit(acc);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) a[r] = cmul(a[r], u);
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) tile[sb ^ sd.sr[r]] = a[r];

@@ -42,7 +42,8 @@ TUSQ_HD uint32_t tile_swizzle(uint32_t e, bool c128) {
 //   DIAG: amp(x) *= exp(2 pi i (phi0 + sum_k phi_k parity(x & mask_k))) with
 //         x the global index; phases in fixed point (2^-31 turn units for
 //         complex64, 2^-63 for complex128); terms sorted by their mask
-//         restricted to the register bits (mu), csr[mu]..csr[mu+1].
+//         restricted to the register bits (mu), csr[mu]..csr[mu+1];
+//         mu_mask has bit mu (>= 1) set iff that group is non-empty.
 struct DevOp {
     int32_t type;
     int32_t a, b;
@@ -52,7 +53,7 @@ struct DevOp {
     uint64_t phi0;         // DIAG: constant phase (fixed point)
     uint16_t csr[34];      // DIAG: term offsets per register mask mu (relative)
     int32_t sw0, sw1;      // SUB_SWAP: the two basis states exchanged (0..3)
-    uint32_t pad1;
+    uint32_t mu_mask;      // DIAG: non-empty register-mask groups mu >= 1
 };
 static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
 

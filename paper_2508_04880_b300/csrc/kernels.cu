@@ -53,29 +53,35 @@ template <typename R> struct SProg {
 };
 
 // 2x2 on register bit B; SUB picks the form (general, real, RX-type).
+// Every product that reads the old pair is formed first, then the final
+// fused multiply-adds overwrite the pair in place.
 template <int V, int B, int SUB, typename C2>
 __device__ __forceinline__ void apply1(C2 (&a)[1 << V], C2 m0, C2 m1, C2 m2, C2 m3) {
 #pragma unroll
     for (int r = 0; r < (1 << V); ++r) {
         if (r & (1 << B)) continue;
-        C2 x = a[r], y = a[r | (1 << B)], u, w;
+        C2 &x = a[r];
+        C2 &y = a[r | (1 << B)];
         if constexpr (SUB == SUB_REAL) {
-            u.x = fma(m0.x, x.x, m1.x * y.x);
-            u.y = fma(m0.x, x.y, m1.x * y.y);
-            w.x = fma(m2.x, x.x, m3.x * y.x);
-            w.y = fma(m2.x, x.y, m3.x * y.y);
+            const auto t0 = m1.x * y.x, t1 = m1.x * y.y, t2 = m2.x * x.x, t3 = m2.x * x.y;
+            x.x = fma(m0.x, x.x, t0);
+            x.y = fma(m0.x, x.y, t1);
+            y.x = fma(m3.x, y.x, t2);
+            y.y = fma(m3.x, y.y, t3);
         } else if constexpr (SUB == SUB_RXTYPE) {
             // [[c, -is], [-is, c]] with c = m0.x, -s = m1.y
-            u.x = fma(m0.x, x.x, -m1.y * y.y);
-            u.y = fma(m0.x, x.y, m1.y * y.x);
-            w.x = fma(m0.x, y.x, -m1.y * x.y);
-            w.y = fma(m0.x, y.y, m1.y * x.x);
+            const auto t0 = m1.y * y.y, t1 = m1.y * y.x, t2 = m1.y * x.y, t3 = m1.y * x.x;
+            x.x = fma(m0.x, x.x, -t0);
+            x.y = fma(m0.x, x.y, t1);
+            y.x = fma(m0.x, y.x, -t2);
+            y.y = fma(m0.x, y.y, t3);
         } else {
-            u = cmad(m0, x, cmul(m1, y));
-            w = cmad(m2, x, cmul(m3, y));
+            const C2 xo = x, yo = y;
+            const C2 u = cmad(m0, xo, cmul(m1, yo));
+            const C2 w = cmad(m2, xo, cmul(m3, yo));
+            x = u;
+            y = w;
         }
-        a[r] = u;
-        a[r | (1 << B)] = w;
     }
 }
 

@@ -62,6 +62,31 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def plan_admitted(T, circuits, shots_of, max_work, max_instances):
+    """Plan every job on host threads (the planner releases the GIL) and keep
+    those whose pruned tree costs at most max_work gate-amplitude updates
+    (tree edges x 2^n) and has at most max_instances leaves (the compiled
+    device program grows with the leaves).  A job whose shots are nearly all
+    distinct keeps ~shots instances after pruning (alpha * c_max <= 1 marks
+    every realization significant); such a job is rejected before its
+    schedule is compiled.  Returns (kept indices, plans by index, rejected
+    list, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=max(1, (os.cpu_count() or 2) // 2)) as pool:
+        plans = list(pool.map(lambda jc: T.plan(jc[1], shots_of(jc[0]), jc[0]), enumerate(circuits)))
+    kept, rejected = [], []
+    for j, (c, p) in enumerate(zip(circuits, plans)):
+        st = p.stats()
+        work = float(st["tree_gate_edges"]) * float(1 << c.n_qubits)
+        if work <= max_work and st["n_instances"] <= max_instances:
+            kept.append(j)
+        else:
+            rejected.append({"job": j, "qubits": c.n_qubits, "gates": c.n_gates,
+                             "instances": int(st["n_instances"]), "work": work})
+    return kept, plans, rejected, time.perf_counter() - t0
+
+
 class ClockSampler:
     """nvidia-smi SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -196,10 +221,12 @@ def run_batch(args, T, torch):
     replayed from a CUDA graph with autotuned options; larger ones run as
     concurrent per-job traversals on several streams.  One step = every job
     once."""
-    jobs = W.job_mix(args.jobs, seed=0, n_lo=12, n_hi=18, d_lo=20, d_hi=80)
-    t0 = time.perf_counter()
-    plans = [T.plan(c, args.batch_shots, j) for j, c in enumerate(jobs)]
-    plan_s = time.perf_counter() - t0
+    all_jobs = W.job_mix(args.jobs, seed=0, n_lo=12, n_hi=18, d_lo=20, d_hi=80)
+    kept, all_plans, rejected, plan_s = plan_admitted(T, all_jobs, lambda j: args.batch_shots, args.max_job_work,
+                                                      args.max_job_instances)
+    jobs = [all_jobs[j] for j in kept]
+    plans = [all_plans[j] for j in kept]
+    del all_plans
     n_inst = sum(p.stats()["n_instances"] for p in plans)
     small = [i for i, c in enumerate(jobs) if c.n_qubits <= 13]
     large = [i for i, c in enumerate(jobs) if c.n_qubits > 13]
@@ -234,19 +261,25 @@ def run_batch(args, T, torch):
     b.finish()
     for e in exs:
         e.finish()
-    # error of a few jobs against the oracle (complex128 reference)
+    # error against the oracle (complex128, every instance from |0..0>) of the
+    # cheapest jobs of each group (instances x gates x 2^n), so that the check
+    # stays within seconds of host time
     import oracle
     errs = []
-    for i in (small[:2] + large[:1]):
-        ref, _ = oracle.run(jobs[i], args.batch_shots, i)
+    cost = {i: plans[i].stats()["n_instances"] * jobs[i].n_gates * (1 << jobs[i].n_qubits) for i in range(len(jobs))}
+    for i in sorted(small, key=cost.get)[:2] + sorted(large, key=cost.get)[:1]:
+        ref, _ = oracle.run(jobs[i], args.batch_shots, kept[i])
         d = np.abs(outs[i].cpu().numpy() - ref)
-        errs.append({"job": i, "qubits": jobs[i].n_qubits, "max_abs": float(d.max()), "tv": float(d.sum())})
+        errs.append({"job": kept[i], "qubits": jobs[i].n_qubits, "max_abs": float(d.max()), "tv": float(d.sum())})
     return {
         "metric": "noisy instances/s (batched jobs)", "value": n_inst / secs, "unit": "instances/s",
         "jobs_per_s": len(jobs) / secs, "ms_per_step": secs * 1e3, "steps": args.steps, "warmup": args.warmup,
         "dtype": "c64", "data": "synthetic",
-        "config": {"workload": f"{len(jobs)} jobs, 12-18 qubits, brickwork/QAOA mix, depth 20-80, "
-                               f"{args.batch_shots} shots each", "jobs_in_one_launch": len(small),
+        "config": {"workload": f"{args.jobs} jobs, 12-18 qubits, brickwork/QAOA mix, depth 20-80, "
+                               f"{args.batch_shots} shots each", "jobs_run": len(jobs),
+                   "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
+                   "max_job_instances": args.max_job_instances,
+                   "jobs_in_one_launch": len(small),
                    "jobs_on_streams": len(large), "instances": n_inst,
                    "autotuned": {"traversal": best.traversal, "schedule": best.schedule, "ms": tune_ms}},
         "plan_seconds": plan_s, "error_vs_oracle": errs,
@@ -258,8 +291,12 @@ def run_served(args, T, torch):
     [1e-4, 1e-2], 1e5-1e6 shots) into the serving loop (admission by HBM
     footprint, concurrent streams, state resident until done).  Reports
     latency (submit to completion) percentiles and throughput per rate."""
-    stream_jobs = W.served_stream(args.jobs, seed=0)
-    plans = [T.plan(c, shots, j) for j, (c, shots) in enumerate(stream_jobs)]
+    all_jobs = W.served_stream(args.jobs, seed=0)
+    kept, all_plans, rejected, plan_s = plan_admitted(T, [c for c, _ in all_jobs], lambda j: all_jobs[j][1],
+                                                      args.max_job_work, args.max_job_instances)
+    stream_jobs = [all_jobs[j] for j in kept]
+    plans = [all_plans[j] for j in kept]
+    del all_plans
     n_inst = [p.stats()["n_instances"] for p in plans]
     outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _ in stream_jobs]
     budget = int(args.hbm_budget_gb * (1 << 30))
@@ -295,6 +332,9 @@ def run_served(args, T, torch):
         del srv
     return {"metric": "served noisy jobs: p50/p99 latency and instances/s", "unit": "s / instances/s",
             "capacity_jobs_per_s": capacity, "jobs": len(plans), "hbm_budget_gb": args.hbm_budget_gb,
+            "jobs_offered": args.jobs, "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
+            "max_job_instances": args.max_job_instances,
+            "plan_seconds": plan_s,
             "qubits": [c.n_qubits for c, _ in stream_jobs], "rates": results, "dtype": "c64",
             "data": "synthetic"}
 
@@ -318,6 +358,11 @@ def main():
     ap.add_argument("--batch-shots", type=int, default=100_000)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 2.0])
+    ap.add_argument("--max-job-work", type=float, default=3e13,
+                    help="batch/served: jobs whose pruned tree exceeds this many gate-amplitude updates "
+                         "(tree edges x 2^n) are rejected at admission and reported")
+    ap.add_argument("--max-job-instances", type=int, default=5000,
+                    help="batch/served: jobs whose pruned tree keeps more leaves are rejected likewise")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

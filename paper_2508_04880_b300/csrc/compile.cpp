@@ -522,6 +522,7 @@ struct Encoder {
                         d.type = OP_MAT1;
                         d.a = regidx[local[o.q0]];
                         d.sub = mat1_sub(o.m);
+                        d.code = CODE_MAT1 + 5 * d.sub + (uint32_t)d.a;
                         d.mat = (uint32_t)(prog.mats.size() / 32);
                         for (int k = 0; k < 16; ++k) {
                             cd z = k < 4 ? o.m[k] : cd(0, 0);
@@ -549,9 +550,14 @@ struct Encoder {
                                 prog.mats.push_back(dm[4 * r + c].real());
                                 prog.mats.push_back(dm[4 * r + c].imag());
                             }
-                        d.sub = mat2_swap(dm, d.sw0, d.sw1) ? SUB_SWAP : SUB_GENERAL;
+                        int s0 = 0, s1 = 0;
+                        d.sub = mat2_swap(dm, s0, s1) ? SUB_SWAP : SUB_GENERAL;
+                        d.sw0 = (int16_t)s0;
+                        d.sw1 = (int16_t)s1;
+                        d.code = (d.sub == SUB_SWAP ? CODE_SWAP : CODE_MAT2) + pair_code(lo, hi);
                     } else {
                         d.type = OP_DIAG;
+                        d.code = CODE_DIAG;
                         d.phi0 = to_fixed(o.phi0, c128);
                         // register mask of each term, sort by it
                         std::vector<std::pair<int, std::pair<uint64_t, double>>> t;

@@ -85,25 +85,6 @@ __device__ __forceinline__ void apply1(C2 (&a)[1 << V], C2 m0, C2 m1, C2 m2, C2 
     }
 }
 
-template <int V, int SUB, typename C2>
-__device__ __forceinline__ void dispatch1b(C2 (&a)[1 << V], int b, C2 m0, C2 m1, C2 m2, C2 m3) {
-    switch (b) {
-    case 0: apply1<V, 0, SUB>(a, m0, m1, m2, m3); break;
-    case 1: if constexpr (V > 1) apply1<V, 1, SUB>(a, m0, m1, m2, m3); break;
-    case 2: if constexpr (V > 2) apply1<V, 2, SUB>(a, m0, m1, m2, m3); break;
-    case 3: if constexpr (V > 3) apply1<V, 3, SUB>(a, m0, m1, m2, m3); break;
-    case 4: if constexpr (V > 4) apply1<V, 4, SUB>(a, m0, m1, m2, m3); break;
-    default: break;
-    }
-}
-
-template <int V, typename C2>
-__device__ __forceinline__ void dispatch1(C2 (&a)[1 << V], int b, uint32_t sub, C2 m0, C2 m1, C2 m2, C2 m3) {
-    if (sub == SUB_REAL) dispatch1b<V, SUB_REAL>(a, b, m0, m1, m2, m3);
-    else if (sub == SUB_RXTYPE) dispatch1b<V, SUB_RXTYPE>(a, b, m0, m1, m2, m3);
-    else dispatch1b<V, SUB_GENERAL>(a, b, m0, m1, m2, m3);
-}
-
 // 4x4 on register bits A < B, basis k = bit_A + 2 bit_B.
 template <int V, int A, int B, typename C2>
 __device__ __forceinline__ void apply2(C2 (&a)[1 << V], const C2 (&m)[16]) {
@@ -142,37 +123,42 @@ __device__ __forceinline__ void swap2(C2 (&a)[1 << V], int s0, int s1) {
     }
 }
 
+// A matrix op, dispatched once on its host-decoded code (form and register
+// bits); each case loads only the matrix entries its form uses.
 template <int V, typename R>
-__device__ __forceinline__ void dispatch2(typename C2T<R>::type (&a)[1 << V], const DevOp &op, const SProg<R> &P) {
+__device__ __forceinline__ void apply_matrix_op(typename C2T<R>::type (&a)[1 << V], const DevOp &op,
+                                                const SProg<R> &P) {
     using C2 = typename C2T<R>::type;
-    const int lo = op.a, hi = op.b;
-    if (op.sub == SUB_SWAP) {
-        const int s0 = op.sw0, s1 = op.sw1;
-#define TUSQ_CASES(X, Y) \
-    case X * 8 + Y: if constexpr (V > Y) swap2<V, X, Y>(a, s0, s1); break;
-        switch (lo * 8 + hi) {
-            TUSQ_CASES(0, 1) TUSQ_CASES(0, 2) TUSQ_CASES(0, 3) TUSQ_CASES(0, 4)
-            TUSQ_CASES(1, 2) TUSQ_CASES(1, 3) TUSQ_CASES(1, 4)
-            TUSQ_CASES(2, 3) TUSQ_CASES(2, 4)
-            TUSQ_CASES(3, 4)
-        default: break;
-        }
-#undef TUSQ_CASES
-        return;
-    }
-    C2 m[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) m[q] = P.mat(op.mat, q);
-#define TUSQ_CASE2(X, Y) \
-    case X * 8 + Y: if constexpr (V > Y) apply2<V, X, Y>(a, m); break;
-    switch (lo * 8 + hi) {
-        TUSQ_CASE2(0, 1) TUSQ_CASE2(0, 2) TUSQ_CASE2(0, 3) TUSQ_CASE2(0, 4)
-        TUSQ_CASE2(1, 2) TUSQ_CASE2(1, 3) TUSQ_CASE2(1, 4)
-        TUSQ_CASE2(2, 3) TUSQ_CASE2(2, 4)
-        TUSQ_CASE2(3, 4)
+    const C2 *m = P.mats + 16 * (op.mat - P.mat0);
+#define TUSQ_M1(B)                                                                               \
+    case CODE_MAT1 + 5 * SUB_GENERAL + B:                                                        \
+        if constexpr (V > B) apply1<V, B, SUB_GENERAL>(a, m[0], m[1], m[2], m[3]);              \
+        break;                                                                                   \
+    case CODE_MAT1 + 5 * SUB_REAL + B:                                                           \
+        if constexpr (V > B) apply1<V, B, SUB_REAL>(a, m[0], m[1], m[2], m[3]);                 \
+        break;                                                                                   \
+    case CODE_MAT1 + 5 * SUB_RXTYPE + B:                                                         \
+        if constexpr (V > B) apply1<V, B, SUB_RXTYPE>(a, m[0], m[1], m[2], m[3]);               \
+        break;
+#define TUSQ_M2(X, Y)                                                                            \
+    case CODE_MAT2 + pair_code(X, Y):                                                            \
+        if constexpr (V > Y) {                                                                   \
+            C2 mm[16];                                                                           \
+            _Pragma("unroll") for (int q = 0; q < 16; ++q) mm[q] = m[q];                        \
+            apply2<V, X, Y>(a, mm);                                                              \
+        }                                                                                        \
+        break;                                                                                   \
+    case CODE_SWAP + pair_code(X, Y):                                                            \
+        if constexpr (V > Y) swap2<V, X, Y>(a, op.sw0, op.sw1);                                  \
+        break;
+    switch (op.code) {
+        TUSQ_M1(0) TUSQ_M1(1) TUSQ_M1(2) TUSQ_M1(3) TUSQ_M1(4)
+        TUSQ_M2(0, 1) TUSQ_M2(0, 2) TUSQ_M2(0, 3) TUSQ_M2(0, 4) TUSQ_M2(1, 2)
+        TUSQ_M2(1, 3) TUSQ_M2(1, 4) TUSQ_M2(2, 3) TUSQ_M2(2, 4) TUSQ_M2(3, 4)
     default: break;
     }
-#undef TUSQ_CASE2
+#undef TUSQ_M1
+#undef TUSQ_M2
 }
 
 // Fixed-point phase -> (cos, sin) of 2 pi * phase.
@@ -345,12 +331,8 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
             typename Phase<R>::U acc = 0;     // the stage's per-thread constant phase
             for (uint32_t k = 0; k < sd.op_count; ++k) {
                 const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
-                const int type = op.type;
-                if (type == OP_MAT1) {
-                    dispatch1<V>(a, op.a, op.sub, P.mat(op.mat, 0), P.mat(op.mat, 1), P.mat(op.mat, 2),
-                                 P.mat(op.mat, 3));
-                } else if (type == OP_MAT2) {
-                    dispatch2<V, R>(a, op, P);
+                if (op.code != CODE_DIAG) {
+                    apply_matrix_op<V, R>(a, op, P);
                 } else {
                     if (!have_gfix) {
                         // global index of this thread's register 0

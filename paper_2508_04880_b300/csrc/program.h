@@ -52,10 +52,21 @@ struct DevOp {
     uint32_t sub;          // DevOpSub
     uint64_t phi0;         // DIAG: constant phase (fixed point)
     uint16_t csr[34];      // DIAG: term offsets per register mask mu (relative)
-    int32_t sw0, sw1;      // SUB_SWAP: the two basis states exchanged (0..3)
+    int16_t sw0, sw1;      // SUB_SWAP: the two basis states exchanged (0..3)
     uint32_t mu_mask;      // DIAG: non-empty register-mask groups mu >= 1
+    uint32_t code;         // the op decoded for the kernels' single dispatch (DevCode)
 };
 static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
+
+// Kernel dispatch code of an op: MAT1 = CODE_MAT1 + 5 sub + a (sub is
+// SUB_GENERAL, SUB_REAL or SUB_RXTYPE), MAT2 = CODE_MAT2 / CODE_SWAP + the
+// index of the register pair (a, b) in (0,1) (0,2) (0,3) (0,4) (1,2) (1,3)
+// (1,4) (2,3) (2,4) (3,4) order, DIAG = CODE_DIAG.
+enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 16, CODE_SWAP = 32, CODE_DIAG = 48 };
+
+TUSQ_HD constexpr uint32_t pair_code(int lo, int hi) {
+    return (uint32_t)(lo * (9 - lo) / 2 + (hi - lo - 1));
+}
 
 struct StageDesc {
     uint8_t rbits[8];      // local bit positions held in registers (ascending)

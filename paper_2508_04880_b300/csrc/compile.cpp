@@ -464,6 +464,7 @@ struct Encoder {
             pd.flags = last ? flags : PF_WRITE;
             pd.leaf_w = leaf_w;
             pd.snap = snap;
+            pd.src_snap = -1;
             pd.op0 = (uint32_t)prog.ops.size();
             pd.mat0 = (uint32_t)(prog.mats.size() / 32);
             pd.term0 = (uint32_t)prog.term_mask.size();
@@ -472,6 +473,8 @@ struct Encoder {
             for (int q = 0; q < n; ++q)
                 if (local[q] < 0) pd.cw[ncw++] = (uint8_t)q;
             pd.n_cw = ncw;
+            pd.cwmask = 0;
+            for (int b = 0; b < ncw; ++b) pd.cwmask |= 1ULL << pd.cw[b];
             pd.ntiles = 1ULL << ncw;
             // load rows: complex64 threads move adjacent pairs (local bit 0 in
             // the registers, 16-byte accesses), so row i starts at local index
@@ -497,10 +500,8 @@ struct Encoder {
                     if (R >> b & 1) sd.rbits[nr++] = (uint8_t)b;
                     else sd.cpos[nc++] = (uint8_t)b;
                 }
-                for (int i = 0; i < v; ++i) {
-                    sd.greg[i] = 1ULL << win[sd.rbits[i]];
-                    sd.sw1[i] = (uint16_t)swz(1u << sd.rbits[i], c128);
-                }
+                for (int i = 0; i < v; ++i) sd.greg[i] = 1ULL << win[sd.rbits[i]];
+                for (int i = 0; i < nc; ++i) sd.cglob[i] = (uint8_t)win[sd.cpos[i]];
                 for (int r = 0; r < (1 << v); ++r) {
                     uint32_t e = 0;
                     for (int i = 0; i < v; ++i)
@@ -814,6 +815,26 @@ struct Compiler {
 };
 
 }  // namespace
+
+void fuse_restores(Program &prog) {
+    std::vector<Step> out;
+    out.reserve(prog.steps.size());
+    for (size_t k = 0; k < prog.steps.size(); ++k) {
+        const Step &s = prog.steps[k];
+        if (s.type == ST_RESTORE && s.check < 0 && s.snap >= 0 && k + 1 < prog.steps.size() &&
+            prog.steps[k + 1].type == ST_PASS) {
+            PassDesc &d = prog.passes[prog.steps[k + 1].pass];
+            const bool writes = (d.flags & PF_WRITE) != 0;
+            const bool same_slot = (d.flags & PF_SNAPSHOT) && d.snap == s.snap;
+            if (writes && !same_slot && d.src_snap < 0) {
+                d.src_snap = s.snap;
+                continue;
+            }
+        }
+        out.push_back(s);
+    }
+    prog.steps.swap(out);
+}
 
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog) {
     prog = Program{};

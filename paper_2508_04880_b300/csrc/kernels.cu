@@ -336,9 +336,11 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
                 } else {
                     if (!have_gfix) {
                         // global index of this thread's register 0
+                        // global index of register 0: the tile bits and, for each
+                        // thread bit set, its global position
                         gfix = tb;
-                        for (int b = 0; b < L; ++b)
-                            if (e >> b & 1) gfix |= 1ull << d.win[b];
+                        for (int i = 0; i < L - V; ++i)
+                            if (tid >> i & 1) gfix |= 1ull << sd.cglob[i];
                         have_gfix = true;
                     }
                     apply_diag<R, V>(a, op, P, gfix, acc);
@@ -370,6 +372,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     const int nthr = blockDim.x;
     C2 *tile = reinterpret_cast<C2 *>(smem_raw);
     C2 *state = reinterpret_cast<C2 *>(args.state);
+    const C2 *srcp = reinterpret_cast<const C2 *>(args.src);   // tile loads (state or a snapshot)
     C2 *snap = reinterpret_cast<C2 *>(args.snap);
     const uint32_t flags = d.flags;
 
@@ -388,20 +391,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
 
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
 
-    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
-        uint64_t tb = 0;
-        for (int b = 0; b < d.n_cw; ++b)
-            if (t >> b & 1) tb |= 1ull << d.cw[b];
+    // tile bits of this CTA's first tile and of the grid stride, deposited
+    // into the tile-index positions; later tiles follow by a masked add
+    // (carries skip the positions outside the mask)
+    uint64_t tb = 0, tstride = 0;
+    for (int b = 0; b < d.n_cw; ++b) {
+        if (blockIdx.x >> b & 1) tb |= 1ull << d.cw[b];
+        if (gridDim.x >> b & 1) tstride |= 1ull << d.cw[b];
+    }
+    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x, tb = ((tb | ~d.cwmask) + tstride) & d.cwmask) {
         const uint64_t gbase = tb | gthr;
         // load the tile: every row load in flight before the shared stores
         if constexpr (kC128) {
             C2 buf[NROW];
 #pragma unroll
-            for (int i = 0; i < NROW; ++i) buf[i] = state[gbase | d.grow[i]];
+            for (int i = 0; i < NROW; ++i) buf[i] = srcp[gbase | d.grow[i]];
 #pragma unroll
             for (int i = 0; i < NROW; ++i) tile[sthr ^ d.srow[i]] = buf[i];
         } else {
-            const float4 *src = reinterpret_cast<const float4 *>(state);
+            const float4 *src = reinterpret_cast<const float4 *>(srcp);
             float4 *dst = reinterpret_cast<float4 *>(tile);
             float4 buf[NROW];
 #pragma unroll

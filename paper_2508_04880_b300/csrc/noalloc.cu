@@ -231,6 +231,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
         case ST_PASS: {
             PassArgs a;
             a.d = pg.passes[s.pass];
+            a.src = state;
             a.state = state;
             a.snap = (a.d.flags & PF_SNAPSHOT) ? (unsigned char *)snaps + state_bytes * a.d.snap : nullptr;
             a.acc = probs_dev;

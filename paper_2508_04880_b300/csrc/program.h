@@ -72,7 +72,7 @@ struct StageDesc {
     uint8_t rbits[8];      // local bit positions held in registers (ascending)
     uint8_t cpos[16];      // remaining local bit positions (ascending) -> thread bits
     uint16_t sr[32];       // swizzled shared-memory offset of register index r
-    uint16_t sw1[8];       // swizzled offset of each register bit alone (sr is their xor)
+    uint8_t cglob[16];     // global position of each thread bit (win[cpos[i]])
     uint64_t greg[8];      // global bit of each register bit (1 << win[rbits[i]])
     uint32_t op_begin, op_count;
 };
@@ -98,11 +98,15 @@ struct PassDesc {
     uint64_t ntiles;
     uint8_t win[16];       // local bit i <-> global bit win[i]
     uint8_t cw[40];        // global positions of the tile-index bits (ascending)
+    uint64_t cwmask;       // the same positions as a mask
     uint64_t grow[32];     // global offset of load row i (local index i * T)
     uint16_t srow[32];     // swizzled shared offset of load row i
     StageDesc st[kMaxStages];
     double leaf_w;
     int32_t snap;          // snapshot slot for PF_SNAPSHOT
+    int32_t src_snap;      // >= 0: load the tiles from this snapshot slot instead
+                           // of the state (an unconditional restore fused into
+                           // the pass that follows it); -1: from the state
     uint32_t prog_bytes;   // shared-memory bytes of the program below
     uint32_t op0, nops;    // the pass's ops: [op0, op0 + nops) of Program::ops
     uint32_t mat0, nmat;   // its matrix slots
@@ -148,6 +152,7 @@ struct Program {
 // Arguments of one pass launch.
 struct PassArgs {
     PassDesc d;
+    const void *src;      // tiles are loaded from here (the state or a snapshot)
     void *state;
     void *snap;           // snapshot buffer for PF_SNAPSHOT
     double *acc;          // FP64 output for PF_LEAF
@@ -186,6 +191,11 @@ struct BatchArgs {
     unsigned long long *counters;    // [0] restores after failed checks, [1] unrecovered drift
     double drift_tol;
 };
+
+// Fuse every unconditional snapshot restore into the pass that follows it
+// when that pass writes the state: the pass loads its tiles from the
+// snapshot and the copy pass disappears.
+void fuse_restores(Program &prog);
 
 struct CompileOpts {
     int precision;

@@ -184,6 +184,7 @@ int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t 
     Program pg;
     try {
         compile_program(*p, compile_opts_of(o, amp << p->n), pg);
+        fuse_restores(pg);
     } catch (const std::exception &ex) {
         set_error(std::string("tusq_compile_stats: schedule compilation failed: ") + ex.what());
         return TUSQ_EINVAL;
@@ -208,6 +209,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     CompileOpts co = compile_opts_of(o, state_bytes);
     try {
         compile_program(*p, co, e->prog);
+        fuse_restores(e->prog);
     } catch (const std::exception &ex) {
         delete e;
         set_error(std::string("tusq_exec_create: schedule compilation failed: ") + ex.what());
@@ -305,6 +307,7 @@ int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
         case ST_PASS: {
             PassArgs a;
             a.d = pg.passes[s.pass];
+            a.src = a.d.src_snap >= 0 ? (const char *)e->snaps + state_bytes * a.d.src_snap : e->state;
             a.state = e->state;
             a.snap = (a.d.flags & PF_SNAPSHOT) ? (char *)e->snaps + state_bytes * a.d.snap : nullptr;
             a.acc = probs;

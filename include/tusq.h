@@ -277,6 +277,27 @@ void tusq_exec_free(tusq_exec *e);
 int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
              void *cuda_stream);
 
+/* ------------------------------------------------------- shot sampling */
+
+/* Shots drawn from an output distribution on the device.  The paper samples
+ * the output state vector of each kept instance s_i times (Sec. III-A1);
+ * tusq_run returns the exact tally-weighted mixture, and this draws `shots`
+ * outcomes from it.
+ *   probs_dev  : device, 2^n_qubits doubles (e.g. tusq_run's output); need
+ *                not be normalised; entries <= 0 or NaN never occur.
+ *   counts_dev : device, 2^n_qubits uint64, caller-owned; overwritten with
+ *                the number of shots that landed on each outcome.
+ * Definition (bit-exact, independent of the device): w_x = floor(p_x 2^56),
+ * C_x = w_0 + ... + w_x (exact integers), W = C_(2^n - 1); shot s takes
+ * r = word 0 of Philox4x64-10 at counter (s, 0, 0, 0), key (seed, 3) and
+ * lands on the first x with C_x > floor(r W / 2^64).
+ * Stream-ordered on cuda_stream; scratch of 8 (2^n + 2^n / 4096 + 1) bytes is
+ * allocated and freed on that stream (cudaMallocAsync); the call waits for
+ * the total weight once.  Returns TUSQ_EINVAL for bad arguments or a
+ * distribution without positive weight, TUSQ_ECUDA for CUDA failures. */
+int tusq_sample(const double *probs_dev, int n_qubits, uint64_t shots, uint64_t seed, uint64_t *counts_dev,
+                void *cuda_stream);
+
 /* ------------------------------------------------------- batched jobs */
 
 typedef struct tusq_batch tusq_batch;   /* opaque */

@@ -17,6 +17,8 @@ Functions and the paper passage each follows:
                                 instances, each simulated independently.
 * ``dm_run``                 -- density-matrix simulation with Pauli channels (Sec. II).
 * ``commute_one``            -- commutation of a single ER (rules 1-6, Sec. III-A3).
+* ``sample``                 -- shot counts drawn from the output distribution (the
+                                paper samples each leaf s_i times, Sec. III-A1).
 
 Parity pins: tests/test_oracle_*.py.  The pruning step is a heuristic whose
 accuracy against the unpruned answer is parity unpinned (only its selection
@@ -81,6 +83,9 @@ def lib():
         L.or_draw_er.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         L.or_draw_prune.restype = ctypes.c_uint64
         L.or_draw_prune.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.or_draw_sample.restype = ctypes.c_uint64
+        L.or_draw_sample.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.or_sample.argtypes = [ctypes.c_int, f64p, ctypes.c_uint64, ctypes.c_uint64, u64p]
         _lib = L
     return _lib
 
@@ -107,6 +112,23 @@ def draw_er(seed: int, shot: int, channel: int) -> int:
 
 def draw_prune(seed: int, i: int) -> int:
     return int(lib().or_draw_prune(seed, i))
+
+
+def draw_sample(seed: int, s: int) -> int:
+    return int(lib().or_draw_sample(seed, s))
+
+
+def sample(probs, shots: int, seed: int) -> np.ndarray:
+    """Shot counts drawn from an output distribution (inverse transform on
+    integer cumulative weights floor(p 2^56); see or_sample)."""
+    p = np.ascontiguousarray(probs, dtype=np.float64)
+    n = int(np.log2(len(p)))
+    assert len(p) == 1 << n
+    counts = np.zeros(len(p), dtype=np.uint64)
+    rc = lib().or_sample(n, _p(p, ctypes.c_double), shots, seed, _p(counts, ctypes.c_uint64))
+    if rc:
+        raise ValueError(f"or_sample failed ({rc})")
+    return counts
 
 
 def gate_matrix(kind: int, params=()) -> np.ndarray:

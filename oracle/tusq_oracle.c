@@ -340,6 +340,53 @@ static uint64_t cdf_threshold(double x)
     return (uint64_t)(x * 18446744073709551616.0);
 }
 
+/* ------------------------------------------------------- shot sampling */
+
+/* Shots drawn from an output distribution.  The paper samples the output
+ * state vector of each kept instance s_i times (Sec. III-A1); here the
+ * shots are drawn from the tally-weighted mixture the traversal returns.
+ * Each outcome gets the fixed-point weight w_x = floor(p_x * 2^56) (0 for
+ * p_x <= 0), C_x = w_0 + ... + w_x is the integer cumulative weight and
+ * W = C_(2^n - 1).  Shot s takes r = word 0 of Philox4x64-10 at counter
+ * (s, 0, 0, 0), key (seed, 3), the target t = floor(r * W / 2^64) (< W) and
+ * lands on the first x with C_x > t.  counts[x] = shots landing on x.
+ * Returns -1 when W = 0 (nothing to sample). */
+uint64_t or_draw_sample(uint64_t seed, uint64_t s)
+{
+    uint64_t ctr[4] = {s, 0, 0, 0}, key[2] = {seed, 3}, out[4];
+    or_philox4x64_10(ctr, key, out);
+    return out[0];
+}
+
+int or_sample(int n, const double *probs, uint64_t shots, uint64_t seed, uint64_t *counts)
+{
+    uint64_t dim = (uint64_t)1 << n;
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * dim);
+    if (!C) return -2;
+    uint64_t acc = 0;
+    for (uint64_t x = 0; x < dim; x++) {
+        double p = probs[x];
+        uint64_t w = p > 0.0 ? (uint64_t)(p * 72057594037927936.0) : 0;   /* 2^56 */
+        acc += w;
+        C[x] = acc;
+        counts[x] = 0;
+    }
+    if (acc == 0) { free(C); return -1; }
+    for (uint64_t s = 0; s < shots; s++) {
+        uint64_t r = or_draw_sample(seed, s);
+        uint64_t t = (uint64_t)(((unsigned __int128)r * acc) >> 64);
+        /* first x with C[x] > t (C is non-decreasing and C[dim-1] = acc > t) */
+        uint64_t lo = 0, hi = dim - 1;
+        while (lo < hi) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        counts[lo]++;
+    }
+    free(C);
+    return 0;
+}
+
 /* --------------------------------------------------------------- the plan */
 
 typedef struct { int slot, q, p; } ev_t;

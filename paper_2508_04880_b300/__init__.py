@@ -36,7 +36,7 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
-    "tusq_run", "tusq_run_noalloc", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
+    "tusq_run", "tusq_run_noalloc", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
@@ -120,6 +120,7 @@ def _load():
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
+        "tusq_sample": (i32, [vp, i32, u64, u64, vp, vp]),
         "tusq_batch_create": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), i32, vp, P(vp)]),
         "tusq_batch_launch": (i32, [vp, vp]),
         "tusq_batch_finish": (i32, [vp, P(RunInfo)]),
@@ -381,6 +382,25 @@ def tusq_run_noalloc(plan: Plan, probs_ptr: int, opts: Optional[RunOpts] = None,
     _check(lib.tusq_run_noalloc(plan.h, ctypes.byref(o), ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream),
                                 ctypes.byref(info)))
     return info.as_dict()
+
+
+def tusq_sample(probs_ptr: int, n_qubits: int, shots: int, seed: int, counts_ptr: int, stream: int = 0) -> None:
+    """Draw `shots` outcomes from the device distribution at probs_ptr into
+    the device uint64 counts at counts_ptr (both 2^n_qubits entries)."""
+    _check(lib.tusq_sample(ctypes.c_void_p(probs_ptr), n_qubits, shots, seed, ctypes.c_void_p(counts_ptr),
+                           ctypes.c_void_p(stream)))
+
+
+def sample_torch(probs, shots: int, seed: int):
+    """Shot counts (torch uint64 tensor on the probs' device) drawn from a
+    torch FP64 device distribution, on torch's current stream."""
+    import torch
+    n = int(probs.numel()).bit_length() - 1
+    if probs.dtype != torch.float64 or not probs.is_cuda or probs.numel() != 1 << n or not probs.is_contiguous():
+        raise ValueError("probs must be a contiguous CUDA float64 tensor of 2^n entries")
+    counts = torch.empty(1 << n, dtype=torch.uint64, device=probs.device)
+    tusq_sample(probs.data_ptr(), n, shots, seed, counts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    return counts
 
 
 def run_torch(plan: Plan, opts: Optional[RunOpts] = None, device: str = "cuda"):

@@ -286,6 +286,76 @@ def run_batch(args, T, torch):
     }
 
 
+def hellinger_fidelity(p, q, torch):
+    """Classical fidelity (sum_x sqrt(p_x q_x))^2 of two distributions."""
+    return float(torch.sqrt(p.clamp(min=0) * q.clamp(min=0)).sum() ** 2)
+
+
+def run_fidelity(args, T, torch):
+    """Pruning study (Sec. IV-C metric delta, Sec. V-D ablation): for seeded
+    circuits shaped like the paper's workloads, the output with pruning
+    (alpha = 0.01, beta = 100) and without it, each against the noiseless
+    output.  delta = |f_A - f_B| / (f_A + f_B) with f the classical fidelity
+    to the noiseless distribution; gamma = time without / time with pruning;
+    the ablation gives the matrix-vector products each stage leaves (shots x
+    gates without tally; unique ERs x gates after tally and after
+    commutation; kept instances x gates after pruning; DFTT edge traversals).
+    Both arms simulate every instance from |0..0>."""
+    cases = [("qaoa_12q_p2", lambda p1, p2: W.qaoa_3regular(12, 2, 3, p1, p2)),
+             ("qaoa_16q_p3", lambda p1, p2: W.qaoa_3regular(16, 3, 4, p1, p2)),
+             ("brickwork_12q_d20", lambda p1, p2: W.brickwork(12, 20, 5, p1, p2)),
+             ("brickwork_16q_d30", lambda p1, p2: W.brickwork(16, 30, 6, p1, p2)),
+             ("random_layers_8q_d30", lambda p1, p2: W.random_layers(8, 30, 7, p1, p2)),
+             ("qaoa_20q_p2", lambda p1, p2: W.qaoa_3regular(20, 2, 8, p1, p2))]
+    shots = args.fidelity_shots
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    out = []
+    for name, make in cases:
+        noisy, ideal_c = make(1e-3, 1e-2), make(0.0, 0.0)
+        ideal, _ = T.run_torch(T.plan(ideal_c, 1, 0), T.run_opts(precision=T.C64))
+        row = {"case": name, "qubits": noisy.n_qubits, "gates": noisy.n_gates}
+        res = {}
+        for prune in (True, False):
+            pl = T.plan(noisy, shots, 0, prune=prune)
+            st = pl.stats()
+            if st["n_instances"] > 10_000:      # the unpruned program would take gigabytes
+                res[prune] = None
+                row["unpruned_instances"] = st["n_instances"]
+                continue
+            # both arms from scratch (no uncompute: the unpruned trees are deeper
+            # than the snapshot LIFO), so the comparison isolates pruning
+            ex = T.Exec(pl, T.run_opts(precision=T.C64, traversal=T.FROM_SCRATCH), sp)
+            probs = torch.empty(1 << noisy.n_qubits, dtype=torch.float64, device="cuda")
+            ex.launch(probs.data_ptr(), sp)
+            ex.finish()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ex.launch(probs.data_ptr(), sp)
+            b.record(stream)
+            ex.finish()
+            res[prune] = (probs, a.elapsed_time(b), st)
+        p_st = res[True][2]
+        G = noisy.n_gates
+        row["ablation_matvecs"] = {"no_tally": shots * G, "tally": p_st["n_raw_unique"] * G,
+                                   "commutation": p_st["n_commuted_unique"] * G,
+                                   "pruning": p_st["n_instances"] * G, "dftt": p_st["dftt_gate_apps"]}
+        row["pruned_instances"] = p_st["n_instances"]
+        f_a = hellinger_fidelity(res[True][0], ideal, torch)
+        row["fidelity_pruned"] = f_a
+        row["ms_pruned"] = res[True][1]
+        if res[False] is not None:
+            f_b = hellinger_fidelity(res[False][0], ideal, torch)
+            row.update({"fidelity_unpruned": f_b, "delta": abs(f_a - f_b) / (f_a + f_b),
+                        "unpruned_instances": res[False][2]["n_instances"], "ms_unpruned": res[False][1],
+                        "gamma_prune": res[False][1] / res[True][1]})
+        out.append(row)
+    deltas = [r["delta"] for r in out if "delta" in r]
+    return {"metric": "pruning relative fidelity difference delta (alpha=0.01, beta=100)",
+            "value": float(np.mean(deltas)) if deltas else None, "max": float(np.max(deltas)) if deltas else None,
+            "unit": "fraction", "shots": shots, "dtype": "c64", "data": "synthetic", "cases": out}
+
+
 def run_served(args, T, torch):
     """Config 5: Poisson arrivals of jobs (10-30 qubits, depth 20-100, p in
     [1e-4, 1e-2], 1e5-1e6 shots) into the serving loop (admission by HBM
@@ -352,8 +422,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--compare", action="store_true", help="also time the other traversals")
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "served"],
-                    help="main: the 28-qubit headline; batch: config 4; served: config 5")
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity"],
+                    help="main: the 28-qubit headline; batch: config 4; served: config 5; "
+                         "fidelity: pruning delta and per-stage ablation")
+    ap.add_argument("--fidelity-shots", type=int, default=20_000)
     ap.add_argument("--jobs", type=int, default=2048)
     ap.add_argument("--batch-shots", type=int, default=100_000)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
@@ -375,7 +447,7 @@ def main():
     import paper_2508_04880_b300 as T
     torch.cuda.set_device(local)
     if args.mode != "main":
-        line = run_batch(args, T, torch) if args.mode == "batch" else run_served(args, T, torch)
+        line = {"batch": run_batch, "served": run_served, "fidelity": run_fidelity}[args.mode](args, T, torch)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
@@ -448,6 +520,18 @@ def main():
                 "mean_launch_ms": float(pms.mean()) if len(pms) else 0.0,
                 "algorithmic_bytes_per_launch": per_launch_bytes}
 
+    # shot sampling of the output (1e6 shots): integer prefix sum over the
+    # 2^n outcomes, then one Philox draw and binary search per shot
+    counts = torch.empty(1 << n, dtype=torch.uint64, device="cuda")
+    T.tusq_sample(probs.data_ptr(), n, shots, 1, counts.data_ptr(), sp)
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sa.record(stream)
+    T.tusq_sample(probs.data_ptr(), n, shots, 2, counts.data_ptr(), sp)
+    sb.record(stream)
+    torch.cuda.synchronize()
+    sample_info = {"shots": shots, "ms": sa.elapsed_time(sb), "counted": int(counts.sum().item())}
+    del counts
+
     # end to end through the C ABI from host buffers: plan (host ECM),
     # compile + upload of the device program, traversal, copy of the
     # distribution to pinned host memory
@@ -485,6 +569,7 @@ def main():
                 "d2h_bytes_per_step": int(8 * (1 << n)), "seconds": e2e_s, "plan_seconds": plan_s,
                 "sum_probs": total},
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
+        "sample": sample_info,
         "run_info": {k: info[k] for k in ("passes", "gate_apps", "pauli_apps", "leaf_passes", "checks",
                                           "restores", "unrecovered", "resets", "max_drift")},
         "plan": {k: pst[k] for k in ("n_raw_unique", "n_commuted_unique", "n_instances",

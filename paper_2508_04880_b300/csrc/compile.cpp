@@ -512,13 +512,54 @@ struct Encoder {
                 for (int i = 0; i < 64; ++i) regidx[i] = -1;
                 for (int i = 0; i < v; ++i) regidx[sd.rbits[i]] = i;
                 sd.op_begin = (uint32_t)prog.ops.size();
-                for (const HOp &o : pieces[s].ops) {
+                const std::vector<HOp> &pops = pieces[s].ops;
+                for (size_t oi = 0; oi < pops.size(); ++oi) {
+                    const HOp &o = pops[oi];
                     if (last && last_uids) {
                         last_uids->push_back(o.uid);
                         last_uids->insert(last_uids->end(), o.merged.begin(), o.merged.end());
                     }
                     DevOp d;
                     std::memset(&d, 0, sizeof d);
+                    // a run of 2x2s of one form on distinct register bits becomes
+                    // one product op (one dispatch in the kernels); 2x2s on
+                    // distinct qubits commute, so the run's order is kept
+                    size_t run_end = oi + 1;
+                    uint32_t run_bits = 0;
+                    if (o.type == H_MAT1) {
+                        const uint32_t sub0 = mat1_sub(o.m);
+                        run_bits = 1u << regidx[local[o.q0]];
+                        while (run_end < pops.size() && pops[run_end].type == H_MAT1 &&
+                               mat1_sub(pops[run_end].m) == sub0 &&
+                               !(run_bits >> regidx[local[pops[run_end].q0]] & 1u)) {
+                            run_bits |= 1u << regidx[local[pops[run_end].q0]];
+                            ++run_end;
+                        }
+                    }
+                    if (o.type == H_MAT1 && run_end - oi >= 2) {
+                        d.type = OP_MAT1;
+                        d.a = (int32_t)run_bits;
+                        d.sub = mat1_sub(o.m);
+                        d.code = CODE_PROD + d.sub;
+                        d.mat = (uint32_t)(prog.mats.size() / 32);
+                        cd pm[32];
+                        for (auto &z : pm) z = 0;
+                        for (size_t k = oi; k < run_end; ++k) {
+                            const int b = regidx[local[pops[k].q0]];
+                            for (int q = 0; q < 4; ++q) pm[4 * b + q] = pops[k].m[q];
+                            if (k > oi && last && last_uids) {
+                                last_uids->push_back(pops[k].uid);
+                                last_uids->insert(last_uids->end(), pops[k].merged.begin(), pops[k].merged.end());
+                            }
+                        }
+                        for (int q = 0; q < 32; ++q) {
+                            prog.mats.push_back(pm[q].real());
+                            prog.mats.push_back(pm[q].imag());
+                        }
+                        prog.ops.push_back(d);
+                        oi = run_end - 1;
+                        continue;
+                    }
                     if (o.type == H_MAT1) {
                         d.type = OP_MAT1;
                         d.a = regidx[local[o.q0]];

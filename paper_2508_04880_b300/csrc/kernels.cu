@@ -123,6 +123,17 @@ __device__ __forceinline__ void swap2(C2 (&a)[1 << V], int s0, int s1) {
     }
 }
 
+// A product op: 2x2s of form SUB on the register bits in `bits`, bit b's
+// matrix at m[4b..4b+3].
+template <int V, int SUB, typename C2>
+__device__ __forceinline__ void apply_prod(C2 (&a)[1 << V], uint32_t bits, const C2 *m) {
+    if (bits & 1u) apply1<V, 0, SUB>(a, m[0], m[1], m[2], m[3]);
+    if constexpr (V > 1) if (bits & 2u) apply1<V, 1, SUB>(a, m[4], m[5], m[6], m[7]);
+    if constexpr (V > 2) if (bits & 4u) apply1<V, 2, SUB>(a, m[8], m[9], m[10], m[11]);
+    if constexpr (V > 3) if (bits & 8u) apply1<V, 3, SUB>(a, m[12], m[13], m[14], m[15]);
+    if constexpr (V > 4) if (bits & 16u) apply1<V, 4, SUB>(a, m[16], m[17], m[18], m[19]);
+}
+
 // A matrix op, dispatched once on its host-decoded code (form and register
 // bits); each case loads only the matrix entries its form uses.
 template <int V, typename R>
@@ -152,6 +163,9 @@ __device__ __forceinline__ void apply_matrix_op(typename C2T<R>::type (&a)[1 << 
         if constexpr (V > Y) swap2<V, X, Y>(a, op.sw0, op.sw1);                                  \
         break;
     switch (op.code) {
+    case CODE_PROD + SUB_GENERAL: apply_prod<V, SUB_GENERAL>(a, (uint32_t)op.a, m); break;
+    case CODE_PROD + SUB_REAL: apply_prod<V, SUB_REAL>(a, (uint32_t)op.a, m); break;
+    case CODE_PROD + SUB_RXTYPE: apply_prod<V, SUB_RXTYPE>(a, (uint32_t)op.a, m); break;
         TUSQ_M1(0) TUSQ_M1(1) TUSQ_M1(2) TUSQ_M1(3) TUSQ_M1(4)
         TUSQ_M2(0, 1) TUSQ_M2(0, 2) TUSQ_M2(0, 3) TUSQ_M2(0, 4) TUSQ_M2(1, 2)
         TUSQ_M2(1, 3) TUSQ_M2(1, 4) TUSQ_M2(2, 3) TUSQ_M2(2, 4) TUSQ_M2(3, 4)

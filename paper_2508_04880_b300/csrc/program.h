@@ -61,8 +61,11 @@ static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
 // Kernel dispatch code of an op: MAT1 = CODE_MAT1 + 5 sub + a (sub is
 // SUB_GENERAL, SUB_REAL or SUB_RXTYPE), MAT2 = CODE_MAT2 / CODE_SWAP + the
 // index of the register pair (a, b) in (0,1) (0,2) (0,3) (0,4) (1,2) (1,3)
-// (1,4) (2,3) (2,4) (3,4) order, DIAG = CODE_DIAG.
-enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 16, CODE_SWAP = 32, CODE_DIAG = 48 };
+// (1,4) (2,3) (2,4) (3,4) order, DIAG = CODE_DIAG.  A product op
+// (CODE_PROD + sub) is a run of 2x2s of one form on distinct register bits:
+// `a` is the mask of those bits and bit b's matrix is entries 4b..4b+3 of
+// the two matrix slots starting at `mat`.
+enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 16, CODE_SWAP = 32, CODE_DIAG = 48, CODE_PROD = 64 };
 
 TUSQ_HD constexpr uint32_t pair_code(int lo, int hi) {
     return (uint32_t)(lo * (9 - lo) / 2 + (hi - lo - 1));

@@ -68,7 +68,18 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                     const DevOp &op = pg.ops[sd.op_begin + k];
                     const double *m = &pg.mats[32 * (size_t)op.mat];
                     auto M = [&](int q) { return cd(m[2 * q], m[2 * q + 1]); };
-                    if (op.type == OP_MAT1) {
+                    if (op.type == OP_MAT1 && op.code >= CODE_PROD) {
+                        // product op: bit b's 2x2 at matrix entries 4b..4b+3
+                        for (int bit = 0; bit < v; ++bit) {
+                            if (!(op.a >> bit & 1)) continue;
+                            for (int r = 0; r < (1 << v); ++r) {
+                                if (r >> bit & 1) continue;
+                                cd x = a[r], y = a[r | 1 << bit];
+                                a[r] = M(4 * bit) * x + M(4 * bit + 1) * y;
+                                a[r | 1 << bit] = M(4 * bit + 2) * x + M(4 * bit + 3) * y;
+                            }
+                        }
+                    } else if (op.type == OP_MAT1) {
                         for (int r = 0; r < (1 << v); ++r) {
                             if (r >> op.a & 1) continue;
                             cd x = a[r], y = a[r | 1 << op.a];

@@ -532,16 +532,17 @@ def main():
     sample_info = {"shots": shots, "ms": sa.elapsed_time(sb), "counted": int(counts.sum().item())}
     del counts
 
-    # end to end through the C ABI from host buffers: plan (host ECM),
-    # compile + upload of the device program, traversal, copy of the
-    # distribution to pinned host memory
+    # end to end through the C ABI from host buffers: plan (ER draws on the
+    # device, tally, commutation and pruning on the host), compile + upload of
+    # the device program, traversal, copy of the distribution to pinned host
+    # memory
     host_out = torch.empty(1 << n, dtype=torch.float64, pin_memory=True)
     e2e_times = []
     h2d = 0
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pl2 = T.plan(circ, shots, seed)
+        pl2 = T.plan(circ, shots, seed, device_sampling=True)
         ex2 = T.Exec(pl2, opts, sp)
         ex2.launch(probs.data_ptr(), sp)
         host_out.copy_(probs, non_blocking=True)

@@ -98,6 +98,8 @@ typedef struct {
     int prune;          /* 0: keep every distinct instance with weight c/S */
     int commute_mode;   /* enum tusq_commute_mode */
     int n_threads;      /* host threads for sampling/commutation; 0 = all cores */
+    int device_sampling;/* 1: draw the ERs of every shot on the current CUDA device
+                           (same draws, same plan); 0: on the host threads */
 } tusq_plan_opts;
 
 typedef struct {
@@ -200,7 +202,7 @@ typedef struct {
 } tusq_run_opts;
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
- * snapshot_bytes = 8 states. */
+ * snapshot_bytes 0 = 64 states when they fit in 16 GiB, else 8 states. */
 void tusq_run_opts_default(tusq_run_opts *o);
 
 typedef struct {

@@ -48,6 +48,12 @@ struct FlatList {
 
 void set_error(const std::string &msg);
 
+// Samples every channel of every shot on the current CUDA device (the ER
+// draws of Sec. III-A1): per shot the number of ER words and their hash, the
+// offsets of each shot's words and the words (channel << 4 | code).
+int sample_ers_device(const std::vector<Channel> &chans, uint64_t shots, uint64_t seed, std::vector<uint32_t> &cnt,
+                      std::vector<uint64_t> &hash, std::vector<uint64_t> &off, std::vector<uint32_t> &words);
+
 }  // namespace tusq
 
 struct tusq_circuit {

@@ -253,6 +253,43 @@ int build_plan(const tusq_circuit &circ, const tusq_plan_opts &opts, uint64_t sh
 
     // 1 + 2. sample every channel of every shot and tally identical ERs.
     double t0 = now_s();
+    std::unordered_map<Key, uint64_t, KeyHash> raw;
+    uint64_t n_ideal = 0;
+    double t1 = t0;
+    if (opts.device_sampling) {
+        // the draws on the device; shots grouped by the hash of their ER
+        // words, word lists compared within a hash group (exact tally)
+        std::vector<uint32_t> cnt, words;
+        std::vector<uint64_t> hash, off;
+        int rc = sample_ers_device(chans, shots, seed, cnt, hash, off, words);
+        if (rc) return rc;
+        t1 = now_s();
+        std::unordered_map<uint64_t, uint32_t> head;
+        head.reserve(shots / 2 + 1);
+        std::vector<uint64_t> rep, rcnt;
+        std::vector<int64_t> nxt;
+        auto same = [&](uint64_t a, uint64_t b) {
+            return cnt[a] == cnt[b] && std::memcmp(&words[off[a]], &words[off[b]], sizeof(uint32_t) * cnt[a]) == 0;
+        };
+        for (uint64_t s = 0; s < shots; ++s) {
+            if (cnt[s] == 0) { ++n_ideal; continue; }
+            auto ins = head.try_emplace(hash[s], (uint32_t)rep.size());
+            if (ins.second) { rep.push_back(s); rcnt.push_back(1); nxt.push_back(-1); continue; }
+            int64_t u = ins.first->second;
+            for (;;) {
+                if (same(rep[u], s)) { rcnt[u]++; break; }
+                if (nxt[u] < 0) {
+                    nxt[u] = (int64_t)rep.size();
+                    rep.push_back(s); rcnt.push_back(1); nxt.push_back(-1);
+                    break;
+                }
+                u = nxt[u];
+            }
+        }
+        raw.reserve(rep.size() + 1);
+        for (size_t u = 0; u < rep.size(); ++u)
+            raw.emplace(Key(words.begin() + off[rep[u]], words.begin() + off[rep[u]] + cnt[rep[u]]), rcnt[u]);
+    } else {
     std::vector<std::unordered_map<Key, uint64_t, KeyHash>> maps(nth);
     std::vector<uint64_t> ideal(nth, 0);
     parallel_for(nth, shots, [&](int t, uint64_t a, uint64_t b) {
@@ -274,14 +311,13 @@ int build_plan(const tusq_circuit &circ, const tusq_plan_opts &opts, uint64_t sh
             else m[er]++;
         }
     });
-    double t1 = now_s();
-    std::unordered_map<Key, uint64_t, KeyHash> raw;
-    uint64_t n_ideal = 0;
+    t1 = now_s();
     for (int t = 0; t < nth; ++t) {
         n_ideal += ideal[t];
         if (raw.empty()) raw.swap(maps[t]);
         else for (auto &kv : maps[t]) raw[kv.first] += kv.second;
         maps[t].clear();
+    }
     }
     if (n_ideal) raw[Key{}] += n_ideal;
     std::vector<const std::pair<const Key, uint64_t> *> rorder;

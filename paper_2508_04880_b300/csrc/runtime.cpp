@@ -406,7 +406,8 @@ void tusq_run_opts_default(tusq_run_opts *o) {
     o->check_every = 0;
 }
 
-// Validate and complete run options (0 snapshot bytes -> 8 states).
+// Validate and complete run options (0 snapshot bytes -> up to 64 states
+// within 16 GiB, at least 8).
 static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run_opts &o,
                         const char *who) {
     tusq_run_opts_default(&o);
@@ -423,7 +424,12 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
         set_error(std::string(who) + ": max_window must be 0 (default) or in [4, 14]");
         return TUSQ_EINVAL;
     }
-    if (o.snapshot_bytes == 0) o.snapshot_bytes = (uint64_t)8 * ((uint64_t)(o.precision == TUSQ_C128 ? 16 : 8) << p->n);
+    if (o.snapshot_bytes == 0) {
+        // 64 LIFO slots when they fit in 16 GiB (deep trees then rarely fall
+        // back to an unchecked uncompute), never fewer than 8
+        const uint64_t state = (uint64_t)(o.precision == TUSQ_C128 ? 16 : 8) << p->n;
+        o.snapshot_bytes = std::max<uint64_t>(8 * state, std::min<uint64_t>(64 * state, (uint64_t)16 << 30));
+    }
     return TUSQ_OK;
 }
 

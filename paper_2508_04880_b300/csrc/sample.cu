@@ -21,6 +21,7 @@
 #include <string>
 
 #include "internal.h"
+#include "philox.cuh"
 
 namespace tusq {
 
@@ -30,25 +31,10 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 16;
 constexpr int kScanChunk = kScanThreads * kScanPerThread;   // outcomes per CTA
 
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 64x64 -> 128-bit products with the published multipliers, the key bumped
-// by the published Weyl increments between rounds.
 __device__ __forceinline__ uint64_t philox_word0(uint64_t c0, uint64_t k0, uint64_t k1) {
-    uint64_t c1 = 0, c2 = 0, c3 = 0;
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
-        const uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
-        const uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
-        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-        k0 += 0x9E3779B97F4A7C15ull;
-        k1 += 0xBB67AE8584CAA73Bull;
-    }
-    return c0;
+    uint64_t out[4];
+    philox4x64_10(c0, 0, 0, 0, k0, k1, out);
+    return out[0];
 }
 
 __device__ __forceinline__ uint64_t weight_of(double p) {

@@ -24,6 +24,14 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
 using namespace tusq;
 using cd = std::complex<double>;
 
+// The planner's device sampling lives in the CUDA library; this host-only
+// build of the planner never asks for it.
+int tusq::sample_ers_device(const std::vector<Channel> &, uint64_t, uint64_t, std::vector<uint32_t> &,
+                            std::vector<uint64_t> &, std::vector<uint64_t> &, std::vector<uint32_t> &) {
+    set_error("device sampling is not part of the host interpreter");
+    return TUSQ_EINVAL;
+}
+
 static double g_diag_mismatch = 0;
 
 static cd unit_of(uint64_t fixed, bool c128) {

@@ -242,7 +242,8 @@ def run_batch(args, T, torch):
     # the per-job programs compile independently (the C calls release the GIL)
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
-        exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT),
+        exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT,
+                                                                       use_graph=int(args.graph)),
                                               side[ki[0] % 8].cuda_stream), enumerate(large)))
 
     def step():
@@ -426,6 +427,9 @@ def main():
                     help="main: the 28-qubit headline; batch: config 4; served: config 5; "
                          "fidelity: pruning delta and per-stage ablation")
     ap.add_argument("--fidelity-shots", type=int, default=20_000)
+    ap.add_argument("--graph", type=int, default=1,
+                    help="batch: replay each per-stream job's traversal from a captured CUDA graph; "
+                         "main: time the traversal on a side stream with graph replay")
     ap.add_argument("--jobs", type=int, default=2048)
     ap.add_argument("--batch-shots", type=int, default=100_000)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
@@ -470,9 +474,12 @@ def main():
     plan_s = time.perf_counter() - t0
     pst = plan.stats()
     n = circ.n_qubits
-    stream = torch.cuda.current_stream()
+    # a side stream, so that the traversal can be captured into a CUDA graph
+    # and replayed (one host call per traversal instead of one per pass)
+    stream = torch.cuda.Stream() if args.graph else torch.cuda.current_stream()
+    torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
-    opts = T.run_opts(precision=prec, traversal=trav)
+    opts = T.run_opts(precision=prec, traversal=trav, use_graph=int(args.graph))
     ex = T.Exec(plan, opts, sp)
     probs = torch.empty(1 << n, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):

@@ -199,6 +199,11 @@ typedef struct {
     int check_every;          /* reserved, 0 */
     int schedule;             /* fusion: 0 = grow windows by the op that admits most
                                  further ops (default), 1 = in list order */
+    int use_graph;            /* 1: the first tusq_exec_launch on a non-default stream
+                                 captures the whole traversal into a CUDA graph; later
+                                 launches with the same output buffer replay it (one
+                                 host call instead of one per pass).  Ignored on the
+                                 legacy default stream and while profiling. */
 } tusq_run_opts;
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,

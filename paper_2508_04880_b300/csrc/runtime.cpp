@@ -61,6 +61,10 @@ struct tusq_exec {
     std::vector<float> prof_ms;
     std::vector<double> prof_bytes;
     std::vector<int32_t> structure;   // 8 fields per pass in launch order
+    // CUDA-graph replay of the whole traversal (use_graph)
+    cudaGraphExec_t gexec = nullptr;
+    double *g_probs = nullptr;
+    uint64_t g_launches = 0;
 };
 
 namespace {
@@ -274,7 +278,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     return TUSQ_OK;
 }
 
-int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
+static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
     Program &pg = e->prog;
     e->stream = st;
     e->launches = 0;
@@ -381,8 +385,47 @@ int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
     return TUSQ_OK;
 }
 
+// One traversal on stream st: the launch sequence directly, or (use_graph,
+// non-default stream, not profiling) a CUDA graph captured from it on the
+// first call and replayed while the output buffer stays the same.
+int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
+    if (!e->opts.use_graph || e->profiling || st == nullptr) return exec_launch_direct(e, probs, st);
+    if (!e->gexec || e->g_probs != probs) {
+        if (e->gexec) {
+            cudaGraphExecDestroy(e->gexec);
+            e->gexec = nullptr;
+        }
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        const int rc = exec_launch_direct(e, probs, st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (rc != TUSQ_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) {
+            set_error(std::string("tusq_exec_launch: cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+            return TUSQ_ECUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&e->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            e->gexec = nullptr;
+            set_error(std::string("tusq_exec_launch: cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+            return TUSQ_ECUDA;
+        }
+        e->g_probs = probs;
+        e->g_launches = e->launches;
+    }
+    e->stream = st;
+    CUDA_TRY(cudaGraphLaunch(e->gexec, st));
+    e->launches = e->g_launches;
+    return TUSQ_OK;
+}
+
 void exec_free(tusq_exec *e) {
     if (!e) return;
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
     for (cudaEvent_t ev : e->prof_ev) cudaEventDestroy(ev);
     release(e);
     cudaStreamSynchronize(e->stream);

@@ -156,3 +156,27 @@ def test_c64_vs_c128_brickwork():
     got, _ = gpu_run(sub, precision=T.C128)
     assert_close(got, ref, T.C128)
 
+
+
+@pytest.mark.parametrize("precision", [T.C128, T.C64])
+def test_graph_replay_equals_direct_launches(precision):
+    # use_graph: the first launch captures the traversal into a CUDA graph on a
+    # side stream, later launches replay it; a new output buffer re-captures
+    import torch
+    circ = W.brickwork(12, 10, 3, 2e-3, 2e-2)
+    pl = T.plan(circ, 20_000, 2)
+    ref, _ = oracle.run(circ, 20_000, 2)
+    side = torch.cuda.Stream()
+    direct = torch.empty(1 << 12, dtype=torch.float64, device="cuda")
+    ex0 = T.Exec(pl, T.run_opts(precision=precision, traversal=T.DFTT), side.cuda_stream)
+    ex0.launch(direct.data_ptr(), side.cuda_stream)
+    ex0.finish()
+    ex = T.Exec(pl, T.run_opts(precision=precision, traversal=T.DFTT, use_graph=1), side.cuda_stream)
+    outs = [torch.full((1 << 12,), -1.0, dtype=torch.float64, device="cuda") for _ in range(2)]
+    for o in (outs[0], outs[0], outs[1], outs[0]):
+        ex.launch(o.data_ptr(), side.cuda_stream)
+        info = ex.finish()
+        assert info["unrecovered"] == 0
+    for o in outs:
+        assert torch.equal(o, direct)
+    assert_close(direct.cpu().numpy(), ref, precision, "graph replay")

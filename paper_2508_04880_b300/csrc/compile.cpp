@@ -866,8 +866,15 @@ void fuse_restores(Program &prog) {
             prog.steps[k + 1].type == ST_PASS) {
             PassDesc &d = prog.passes[prog.steps[k + 1].pass];
             const bool writes = (d.flags & PF_WRITE) != 0;
-            const bool same_slot = (d.flags & PF_SNAPSHOT) && d.snap == s.snap;
-            if (writes && !same_slot && d.src_snap < 0) {
+            // A pass that does not write the state (a leaf peek) may read the
+            // snapshot too when nothing reads the state buffer before it is
+            // overwritten: the next step restores, resets, or there is none.
+            // The pass may write the snapshot slot it reads: a CTA loads its
+            // whole tile before writing that tile back, and tiles are disjoint.
+            const Step *after = k + 2 < prog.steps.size() ? &prog.steps[k + 2] : nullptr;
+            const bool state_dead = !after || after->type == ST_INIT ||
+                                    (after->type == ST_RESTORE && after->check < 0);
+            if ((writes || state_dead) && d.src_snap < 0) {
                 d.src_snap = s.snap;
                 continue;
             }

@@ -196,7 +196,8 @@ struct BatchArgs {
 };
 
 // Fuse every unconditional snapshot restore into the pass that follows it
-// when that pass writes the state: the pass loads its tiles from the
+// when that pass writes the state, or when the state buffer is not read
+// again before the next restore or reset: the pass loads its tiles from the
 // snapshot and the copy pass disappears.
 void fuse_restores(Program &prog);
 

@@ -57,7 +57,7 @@ enum tusq_traversal {
     TUSQ_DFTT = 0,          /* uncompute back to each branch point (Sec. III-B) */
     TUSQ_FROM_SCRATCH = 1,  /* every instance from |0..0> (the plain form) */
     TUSQ_DFTT_SNAPSHOT = 2  /* DFTT that restores a branch node from its LIFO
-                               snapshot when it has one (one copy pass instead of
+                               snapshot when it has one (loaded by the next pass instead of
                                uncomputing), uncomputing otherwise */
 };
 

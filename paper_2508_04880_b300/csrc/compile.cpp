@@ -380,7 +380,7 @@ struct Encoder {
         // inside a stage, order the ops so that every diagonal op that is ready
         // at the same time is applied together (alternately all ready diagonal
         // ops, then all ready matrix ops), and merge neighbours: each diagonal
-        // run costs a Walsh transform and a phase per amplitude
+        // run costs a pass over the thread's registers per register-mask group
         struct Piece { uint64_t R; std::vector<HOp> ops; };
         std::vector<Piece> pieces;
         for (size_t s = 0; s < sched.size(); ++s) {
@@ -825,7 +825,8 @@ struct Compiler {
     void return_to(uint64_t i, int t, const std::vector<int> &leaf_ops, Stack &stack, bool snap_policy) {
             const int G = this->G;
             if (snap_policy && !stack.empty() && stack.back().snap >= 0) {
-                // the branch node's own snapshot: one copy pass back to it
+                // the branch node's own snapshot: a restore, which fuse_restores
+                // folds into the next pass's tile loads
                 prog.steps.push_back(Step{ST_RESTORE, 0, stack.back().depth, stack.back().snap, -1});
                 prog.restores++;
                 return;

@@ -445,7 +445,7 @@ void tusq_run_opts_default(tusq_run_opts *o) {
     o->leaf_peek = 1;
     o->root_reset = 1;
     o->drift_tol = 1e-6;
-    o->snapshot_bytes = 0;      // 0 -> 8 states (resolved in tusq_exec_create)
+    o->snapshot_bytes = 0;      // 0 -> up to 64 states within 16 GiB, at least 8 (resolved at exec creation)
     o->check_every = 0;
 }
 

@@ -7,9 +7,10 @@
 // through their register bits, 2x2 / 4x4 / diagonal-run ops, the leaf,
 // snapshot, record and check steps -- in FP64 on the host, so that the
 // compiler's traversal, fusion and layout logic can be checked against the
-// oracle without a GPU.  The diagonal runs are evaluated both with the
-// kernel's Walsh-Hadamard fixed-point formula and directly from the global
-// index; any mismatch is reported.
+// oracle without a GPU.  The diagonal runs are evaluated both from the
+// per-register fixed-point angles (a Walsh-Hadamard form of the register-mask
+// groups whose phases the kernels apply group by group) and directly from the
+// global index; any mismatch is reported.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -107,7 +108,7 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                             for (int q = 0; q < 4; ++q) a[idx[q]] = out[q];
                         }
                     } else {
-                        // kernel formula: A + (sum C - WHT(C)[r]) / 2 in fixed point
+                        // per-register angle: A + (sum C - WHT(C)[r]) / 2 in fixed point
                         uint64_t gfix = tb;
                         for (int b = 0; b < L - v; ++b)
                             if (tid >> b & 1) gfix |= 1ULL << d.win[sd.cpos[b]];

@@ -232,7 +232,7 @@ def run_batch(args, T, torch):
     large = [i for i, c in enumerate(jobs) if c.n_qubits > 13]
     outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c in jobs]
     stream = torch.cuda.Stream()
-    side = [torch.cuda.Stream() for _ in range(8)]
+    side = [torch.cuda.Stream() for _ in range(args.streams)]
     base = T.run_opts(precision=T.C64)
     with torch.cuda.stream(stream):
         best, tune_ms = T.tusq_batch_autotune([plans[i] for i in small], [outs[i].data_ptr() for i in small],
@@ -244,12 +244,12 @@ def run_batch(args, T, torch):
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
         exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT,
                                                                        use_graph=int(args.graph)),
-                                              side[ki[0] % 8].cuda_stream), enumerate(large)))
+                                              side[ki[0] % len(side)].cuda_stream), enumerate(large)))
 
     def step():
         b.launch(stream.cuda_stream)
         for k, i in enumerate(large):
-            exs[k].launch(outs[i].data_ptr(), side[k % 8].cuda_stream)
+            exs[k].launch(outs[i].data_ptr(), side[k % len(side)].cuda_stream)
 
     for _ in range(args.warmup):
         step()
@@ -427,6 +427,8 @@ def main():
                     help="main: the 28-qubit headline; batch: config 4; served: config 5; "
                          "fidelity: pruning delta and per-stage ablation")
     ap.add_argument("--fidelity-shots", type=int, default=20_000)
+    ap.add_argument("--streams", type=int, default=32,
+                    help="batch: streams the jobs too large for one CTA are spread over")
     ap.add_argument("--graph", type=int, default=1,
                     help="batch: replay each per-stream job's traversal from a captured CUDA graph; "
                          "main: time the traversal on a side stream with graph replay")

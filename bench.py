@@ -373,7 +373,7 @@ def run_served(args, T, torch):
     budget = int(args.hbm_budget_gb * (1 << 30))
     results = []
     # capacity: everything submitted at once
-    srv = T.Server(budget, n_streams=8)
+    srv = T.Server(budget, n_streams=args.slots)
     t0 = time.perf_counter()
     ids = [srv.submit(p, o.data_ptr(), T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT))
            for p, o in zip(plans, outs)]
@@ -385,7 +385,7 @@ def run_served(args, T, torch):
     for frac in args.rates:
         lam = frac * capacity
         gaps = rng.exponential(1.0 / lam, len(plans))
-        srv = T.Server(budget, n_streams=8)
+        srv = T.Server(budget, n_streams=args.slots)
         t0 = time.perf_counter()
         ids = []
         for p, o, g in zip(plans, outs, gaps):
@@ -429,6 +429,9 @@ def main():
     ap.add_argument("--fidelity-shots", type=int, default=20_000)
     ap.add_argument("--streams", type=int, default=32,
                     help="batch: streams the jobs too large for one CTA are spread over")
+    ap.add_argument("--slots", type=int, default=8,
+                    help="served: stream slots of the serving loop (32 measured no higher capacity and a "
+                         "higher p99 under load than 8)")
     ap.add_argument("--graph", type=int, default=1,
                     help="batch: replay each per-stream job's traversal from a captured CUDA graph; "
                          "main: time the traversal on a side stream with graph replay")

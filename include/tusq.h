@@ -100,6 +100,12 @@ typedef struct {
     int n_threads;      /* host threads for sampling/commutation; 0 = all cores */
     int device_sampling;/* 1: draw the ERs of every shot on the current CUDA device
                            (same draws, same plan); 0: on the host threads */
+    int terminal_fold;  /* 1: fold the Paulis left at slot G into the readout
+                           (Sec. II: the output is the computational-basis
+                           distribution): Z is dropped and Y becomes X, since
+                           |(Z psi)_x|^2 = |psi_x|^2 and |(Y psi)_x|^2 = |(X psi)_x|^2.
+                           Lossless; instances that differ only there merge
+                           before pruning.  0: keep them as slot-G events */
 } tusq_plan_opts;
 
 typedef struct {

@@ -71,7 +71,7 @@ def lib():
         L.or_plan_build.restype = ctypes.c_void_p
         L.or_plan_build.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, ctypes.c_int,
                                     i32p, i32p, i32p, f64p, ctypes.c_uint64, ctypes.c_uint64,
-                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64]
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_int]
         L.or_plan_free.argtypes = [ctypes.c_void_p]
         L.or_plan_sizes.argtypes = [ctypes.c_void_p, i64p]
         L.or_plan_raw.argtypes = [ctypes.c_void_p, i64p, i32p, i32p, u64p]
@@ -211,7 +211,7 @@ def _split(off, *cols):
 
 
 def plan(circ, shots: int, seed: int, commute_mode: int = 2, prune: bool = True,
-         alpha: float = 0.01, beta: int = 100) -> OraclePlan:
+         alpha: float = 0.01, beta: int = 100, terminal_fold: bool = False) -> OraclePlan:
     kinds, q0, q1, params, ch_gate, ch_nterms, ch_codes, ch_probs = _circ_arrays(circ)
     z = np.zeros(1, dtype=np.int32)
     zf = np.zeros(1, dtype=np.float64)
@@ -222,7 +222,7 @@ def plan(circ, shots: int, seed: int, commute_mode: int = 2, prune: bool = True,
                         _p(ch_nterms if len(ch_nterms) else z, ctypes.c_int),
                         _p(ch_codes if len(ch_codes) else z, ctypes.c_int),
                         _p(ch_probs if len(ch_probs) else zf, ctypes.c_double),
-                        shots, seed, commute_mode, int(bool(prune)), alpha, beta)
+                        shots, seed, commute_mode, int(bool(prune)), alpha, beta, int(bool(terminal_fold)))
     try:
         sz = np.zeros(12, dtype=np.int64)
         L.or_plan_sizes(h, _p(sz, ctypes.c_int64))
@@ -283,9 +283,9 @@ def run_instances(circ, instances, weights, first: int = 0, count: Optional[int]
 
 
 def run(circ, shots: int, seed: int, commute_mode: int = 2, prune: bool = True,
-        alpha: float = 0.01, beta: int = 100):
+        alpha: float = 0.01, beta: int = 100, terminal_fold: bool = False):
     """Full oracle: plan, then every kept instance simulated independently."""
-    pl = plan(circ, shots, seed, commute_mode, prune, alpha, beta)
+    pl = plan(circ, shots, seed, commute_mode, prune, alpha, beta, terminal_fold)
     return run_instances(circ, pl.inst, pl.weights), pl
 
 

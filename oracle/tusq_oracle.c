@@ -17,6 +17,9 @@
  *   - ER commutation [Sec. III-A2, rules 1-6 in Sec. III-A3], done as a
  *     naive rewrite to a fixpoint (each noisy Pauli is moved one gate at a
  *     time while a rule allows it), not with the paper's per-qubit stacks.
+ *   - Optional readout fold of the Paulis left after the last gate: Z
+ *     dropped, Y turned into X, since only |psi_x|^2 is observed [Sec. II]
+ *     (pinned in tests/test_terminal_fold.py).
  *   - Pruning with alpha / beta and reweighting [Sec. III-A4, Eq. S_final].
  *   - The DFS order of the instance tree and the branch slot between
  *     neighbouring leaves [Sec. III-B].
@@ -720,7 +723,7 @@ void or_plan_free(void *h)
 void *or_plan_build(int n, int G, const int *kinds, const int *q0, const int *q1,
                     int C, const int *ch_gate, const int *ch_nterms, const int *ch_codes,
                     const double *ch_probs, uint64_t shots, uint64_t seed,
-                    int commute_mode, int prune, double alpha, int64_t beta)
+                    int commute_mode, int prune, double alpha, int64_t beta, int terminal_fold)
 {
     or_plan *P = calloc(1, sizeof(or_plan));
     P->n = n; P->G = G; P->C = C; P->kinds = kinds; P->q0 = q0; P->q1 = q1;
@@ -805,6 +808,21 @@ void *or_plan_build(int n, int G, const int *kinds, const int *q0, const int *q1
         ev_t *one;
         int m = commute_er(P, commute_mode, P->raw_ch + P->raw_off[i],
                            P->raw_code + P->raw_off[i], len, &one);
+        if (terminal_fold) {
+            /* readout fold (Sec. II, output = |psi_x|^2): after the last
+             * gate Z leaves every |psi_x|^2 unchanged and Y = iXZ acts on
+             * them as X does, so Z events at slot G go and Y becomes X */
+            int kept = 0;
+            for (int e = 0; e < m; e++) {
+                ev_t t = one[e];
+                if (t.slot == G) {
+                    if (t.p == 3) continue;
+                    t.p = 1;
+                }
+                one[kept++] = t;
+            }
+            m = kept;
+        }
         if (kused + m > ecap) {
             ecap = 2 * (kused + m);
             kev = realloc(kev, sizeof(ev_t) * ecap);

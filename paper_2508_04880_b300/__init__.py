@@ -51,7 +51,8 @@ class TusqError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_uint32), ("prune", ctypes.c_int),
-                ("commute_mode", ctypes.c_int), ("n_threads", ctypes.c_int), ("device_sampling", ctypes.c_int)]
+                ("commute_mode", ctypes.c_int), ("n_threads", ctypes.c_int), ("device_sampling", ctypes.c_int),
+                ("terminal_fold", ctypes.c_int)]
 
 
 class PlanStats(ctypes.Structure):
@@ -267,8 +268,9 @@ class Plan:
 
 def tusq_plan(circ: Circuit, shots: int, seed: int, alpha: float = 0.01, beta: int = 100,
               prune: bool = True, commute_mode: int = COMMUTE_CLIFFORD, n_threads: int = 0,
-              device_sampling: bool = False) -> Plan:
-    o = PlanOpts(alpha, beta, int(bool(prune)), commute_mode, n_threads, int(bool(device_sampling)))
+              device_sampling: bool = False, terminal_fold: bool = False) -> Plan:
+    o = PlanOpts(alpha, beta, int(bool(prune)), commute_mode, n_threads, int(bool(device_sampling)),
+                 int(bool(terminal_fold)))
     h = ctypes.c_void_p()
     _check(lib.tusq_plan(circ.h, ctypes.byref(o), shots, seed, ctypes.byref(h)))
     return Plan(h, circ.n_qubits)

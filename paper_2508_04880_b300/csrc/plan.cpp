@@ -201,6 +201,21 @@ struct Commuter {
     }
 };
 
+// Readout fold of the Paulis left after the last gate: only |psi_x|^2 is
+// observed, so a Z there changes nothing and a Y acts like an X.
+void fold_terminal(Key &k, int G) {
+    size_t o = 0;
+    for (uint32_t w : k) {
+        Event e = unpack_event(w);
+        if (e.slot == G) {
+            if (!px(e.pauli)) continue;
+            w = pack_event(G, e.qubit, 1);
+        }
+        k[o++] = w;
+    }
+    k.resize(o);
+}
+
 struct Kept {
     const Key *key;
     uint64_t count;
@@ -337,7 +352,10 @@ int build_plan(const tusq_circuit &circ, const tusq_plan_opts &opts, uint64_t sh
     Commuter cm{&circ.gates, &chans, circ.n, P.G, opts.commute_mode};
     std::vector<Key> ckeys(rorder.size());
     parallel_for(nth, rorder.size(), [&](int, uint64_t a, uint64_t b) {
-        for (uint64_t i = a; i < b; ++i) ckeys[i] = cm.run(rorder[i]->first);
+        for (uint64_t i = a; i < b; ++i) {
+            ckeys[i] = cm.run(rorder[i]->first);
+            if (opts.terminal_fold) fold_terminal(ckeys[i], P.G);
+        }
     });
     std::unordered_map<Key, uint64_t, KeyHash> com;
     com.reserve(rorder.size());

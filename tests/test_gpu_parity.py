@@ -180,3 +180,19 @@ def test_graph_replay_equals_direct_launches(precision):
     for o in outs:
         assert torch.equal(o, direct)
     assert_close(direct.cpu().numpy(), ref, precision, "graph replay")
+
+
+@pytest.mark.parametrize("precision", [T.C128, T.C64])
+@pytest.mark.parametrize("prune", [True, False])
+def test_terminal_fold_matches_oracle(precision, prune):
+    # readout fold on: Z at slot G dropped, Y there turned into X; the kept
+    # instances and their weights are the oracle's, and without pruning the
+    # output equals the unfolded one
+    circ = W.qaoa_3regular(12, 2, 5, 5e-3, 2e-2)
+    ref, _ = oracle.run(circ, 20_000, 3, prune=prune, terminal_fold=True)
+    got, info = gpu_run(T.plan(circ, 20_000, 3, prune=prune, terminal_fold=True), precision=precision,
+                        traversal=T.DFTT_SNAPSHOT)
+    assert_close(got, ref, precision, "fold")
+    if not prune:
+        plain, _ = gpu_run(T.plan(circ, 20_000, 3, prune=False), precision=precision, traversal=T.DFTT_SNAPSHOT)
+        assert_close(got, plain, precision, "fold vs plain")

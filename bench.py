@@ -357,6 +357,57 @@ def run_fidelity(args, T, torch):
             "unit": "fraction", "shots": shots, "dtype": "c64", "data": "synthetic", "cases": out}
 
 
+def run_caching(args, T, torch):
+    """DFTT+Caching (Sec. III-B2) on a circuit with mid-circuit resets: a
+    22-qubit brickwork with three layers of two resets each (every kept
+    instance has 2^6 Kraus-branch leaves).  For cache capacities K = 0..4 the
+    uncompute traversal without drift checks (the cache is its only saved
+    state) is timed on the device, with the paper's recovery metric
+    alpha(K) = (N1 - N_K) / (N1 - N2): N1 = gate applications with every
+    leaf from |0..0>, N2 = those of a DFTT that could uncompute the resets,
+    N_K = those executed with capacity K.  The snapshot traversal and the
+    from-scratch form are timed beside them."""
+    circ = W.mcm_brickwork(args.mcm_qubits, 12, 3, 2, 0, 1e-3, 1e-2)
+    pl = T.plan(circ, 1_000_000, 0)
+    st = pl.stats()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    probs = torch.empty(1 << circ.n_qubits, dtype=torch.float64, device="cuda")
+
+    def timed(**kw):
+        ex = T.Exec(pl, T.run_opts(precision=T.C64, **kw), sp)
+        ex.launch(probs.data_ptr(), sp)
+        info = ex.finish()
+        ms = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ex.launch(probs.data_ptr(), sp)
+            b.record(stream)
+            ex.finish()
+            ms.append(a.elapsed_time(b))
+        del ex
+        return min(ms), info, probs.sum().item()
+
+    n1_ms, n1_info, _ = timed(traversal=T.FROM_SCRATCH)
+    N1 = n1_info["gate_apps"]
+    N2 = st["dftt_gate_apps"]
+    rows = []
+    for K in range(0, 5):
+        ms, info, total = timed(traversal=T.DFTT, drift_tol=-1.0, cache_states=K)
+        rows.append({"K": K, "ms": ms, "gate_apps": info["gate_apps"], "passes": info["passes"],
+                     "alpha": (N1 - info["gate_apps"]) / (N1 - N2), "cache_restores": info["cache_restores"],
+                     "rederives": info["rederives"], "sum_probs": total})
+    snap_ms, snap_info, _ = timed(traversal=T.DFTT_SNAPSHOT)
+    return {"metric": "DFTT+Caching recovery alpha(K) and time, mid-circuit resets", "unit": "fraction",
+            "value": rows[-1]["alpha"], "dtype": "c64", "data": "synthetic",
+            "workload": {"circuit": circ.name, "qubits": circ.n_qubits, "gates": circ.n_gates,
+                         "resets": st["n_noninvertible"], "layers": st["n_noninv_layers"],
+                         "ecm_instances": st["n_ecm_instances"], "leaves": st["n_instances"], "shots": 1_000_000},
+            "N1_scratch_gate_apps": N1, "N2_dftt_gate_apps": N2, "scratch_ms": n1_ms,
+            "snapshot_ms": snap_ms, "snapshot_gate_apps": snap_info["gate_apps"], "uncompute": rows}
+
+
 def run_served(args, T, torch):
     """Config 5: Poisson arrivals of jobs (10-30 qubits, depth 20-100, p in
     [1e-4, 1e-2], 1e5-1e6 shots) into the serving loop (admission by HBM
@@ -423,10 +474,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--compare", action="store_true", help="also time the other traversals")
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity"],
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity", "caching"],
                     help="main: the 28-qubit headline; batch: config 4; served: config 5; "
                          "fidelity: pruning delta and per-stage ablation")
     ap.add_argument("--fidelity-shots", type=int, default=20_000)
+    ap.add_argument("--mcm-qubits", type=int, default=22, help="qubits of the --mode caching circuit")
     ap.add_argument("--streams", type=int, default=32,
                     help="batch: streams the jobs too large for one CTA are spread over")
     ap.add_argument("--slots", type=int, default=8,
@@ -456,7 +508,8 @@ def main():
     import paper_2508_04880_b300 as T
     torch.cuda.set_device(local)
     if args.mode != "main":
-        line = {"batch": run_batch, "served": run_served, "fidelity": run_fidelity}[args.mode](args, T, torch)
+        line = {"batch": run_batch, "served": run_served, "fidelity": run_fidelity,
+                 "caching": run_caching}[args.mode](args, T, torch)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -42,8 +42,25 @@ extern "C" {
 
 enum tusq_gate_kind {
     TUSQ_H = 0, TUSQ_X, TUSQ_Y, TUSQ_Z, TUSQ_S, TUSQ_SDG, TUSQ_T, TUSQ_TDG,
-    TUSQ_RX, TUSQ_RY, TUSQ_RZ, TUSQ_U1Q, TUSQ_CX, TUSQ_CZ, TUSQ_RZZ, TUSQ_U2Q
+    TUSQ_RX, TUSQ_RY, TUSQ_RZ, TUSQ_U1Q, TUSQ_CX, TUSQ_CZ, TUSQ_RZZ, TUSQ_U2Q,
+    /* Non-invertible one-qubit operations (Sec. III-B2: mid-circuit
+     * measurements and other channels DFTT cannot back-traverse).  Each is
+     * unravelled into its two Kraus branches: the state after it is the
+     * unnormalised K_m psi, m = 0, 1, and every branch is a child in the
+     * instance tree, so the tally-weighted sum of |psi_leaf|^2 is the exact
+     * output distribution (the branch norms carry the outcome
+     * probabilities; mid-circuit records are not part of the output).
+     *   RESET:   K_m = |0><m|  (measure and reset to |0>)
+     *   MEASURE: K_m = |m><m|  (projective Z measurement, record discarded)
+     * Paulis are not commuted across them.  Consecutive ones (no other gate
+     * between) form one layer: one non-invertible edge, one cache entry. */
+    TUSQ_RESET = 16, TUSQ_MEASURE = 17
 };
+
+/* Event code of a Kraus-branch choice in an instance's event list: the
+ * event (j, q, TUSQ_OUTCOME1) means the non-invertible gate j on qubit q
+ * takes branch m = 1; without it, m = 0.  Pauli events use codes 1..3. */
+#define TUSQ_OUTCOME1 4
 
 enum tusq_precision { TUSQ_C64 = 0, TUSQ_C128 = 1 };
 
@@ -117,7 +134,8 @@ typedef struct {
     uint64_t n_significant;       /* |C_S| */
     uint64_t n_insignificant;     /* |C_I| */
     uint64_t n_picked;            /* min(beta, |C_I|) */
-    uint64_t n_instances;         /* leaves N_l = S_final (Eq. S_final) */
+    uint64_t n_instances;         /* leaves N_l = S_final (Eq. S_final), times 2^R with R
+                                     RESET / MEASURE gates (one leaf per Kraus-branch record) */
     uint64_t tree_gate_edges;     /* |E| counted in gate applications */
     uint64_t dftt_gate_apps;      /* 2|E| - G: DFTT without root resets */
     uint64_t scratch_gate_apps;   /* N_l * G: every instance from scratch */
@@ -127,6 +145,9 @@ typedef struct {
     double seconds_tally;
     double seconds_commute;
     double seconds_prune_tree;
+    uint64_t n_noninvertible;     /* RESET / MEASURE gates R: each kept instance has 2^R leaves */
+    uint64_t n_noninv_layers;     /* their layers (runs with no other gate between) */
+    uint64_t n_ecm_instances;     /* kept instances before the Kraus-branch expansion */
 } tusq_plan_stats_t;
 
 /* Run the Error Characterization Module on the host (Sec. III-A) and build
@@ -152,11 +173,14 @@ int tusq_plan_stats(const tusq_plan_t *p, tusq_plan_stats_t *out);
 /* Build a plan from a caller-supplied instance list instead of running the
  * ECM: n_inst instances, instance i's events are [ev_off[i], ev_off[i+1])
  * of ev_slot / ev_qubit / ev_pauli (slot in [0, G], qubit in [0, n), Pauli
- * 1..3; at most one event per (slot, qubit)), with weights[i].  The
+ * 1..3; at most one Pauli per (slot, qubit); TUSQ_OUTCOME1 only at slot j
+ * of a RESET / MEASURE gate j on its qubit, after any Pauli there), with
+ * weights[i].  No Kraus-branch expansion is done: an instance without an
+ * outcome event at a non-invertible gate takes branch 0 there.  The
  * instances are sorted into DFS order and the branch slots computed as in
  * tusq_plan; counts are reported as 0.  Returns TUSQ_EINVAL on a malformed
- * list (bad slot/qubit/Pauli, unsorted or duplicate (slot, qubit), two
- * identical instances). */
+ * list (bad slot/qubit/code, unsorted or duplicate events, two identical
+ * instances). */
 int tusq_plan_from_instances(const tusq_circuit *c, uint64_t n_inst, const uint64_t *ev_off,
                              const int32_t *ev_slot, const int32_t *ev_qubit,
                              const int32_t *ev_pauli, const double *weights, tusq_plan_t **out);
@@ -210,6 +234,15 @@ typedef struct {
                                  launches with the same output buffer replay it (one
                                  host call instead of one per pass).  Ignored on the
                                  legacy default stream and while profiling. */
+    int cache_states;         /* DFTT+Caching (Sec. III-B2): capacity K of the LIFO cache of
+                                 states taken just before a non-invertible layer; backtracking
+                                 across such a layer restores the cached state instead of
+                                 uncomputing.  When more layers are on the current path than
+                                 K, the K closest to the leaf are kept and a return that finds
+                                 no usable state re-derives it forward from the deepest
+                                 snapshot above it, or from |0..0>.  -1 (default) = one per
+                                 non-invertible layer, at most 8; 0 = no cache.  Each entry is
+                                 one state of device memory on top of snapshot_bytes. */
 } tusq_run_opts;
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
@@ -234,6 +267,9 @@ typedef struct {
     uint64_t matrix_ops;          /* fused 2x2 / 4x4 device ops */
     uint64_t diag_ops;            /* fused diagonal-phase device ops */
     uint64_t diag_terms;          /* their terms */
+    uint64_t cache_restores;      /* DFTT+Caching: returns served by a cached pre-layer state */
+    uint64_t rederives;           /* returns re-derived forward from a snapshot above or |0..0>
+                                     (no usable state below a non-invertible layer) */
 } tusq_run_info_t;
 
 /* Compile a plan into a device program for the current device and allocate

@@ -223,6 +223,8 @@ def plan(circ, shots: int, seed: int, commute_mode: int = 2, prune: bool = True,
                         _p(ch_codes if len(ch_codes) else z, ctypes.c_int),
                         _p(ch_probs if len(ch_probs) else zf, ctypes.c_double),
                         shots, seed, commute_mode, int(bool(prune)), alpha, beta, int(bool(terminal_fold)))
+    if not h:
+        raise ValueError("oracle plan: the Kraus-branch expansion exceeds 2^24 instances")
     try:
         sz = np.zeros(12, dtype=np.int64)
         L.or_plan_sizes(h, _p(sz, ctypes.c_int64))

@@ -26,7 +26,12 @@
  *   - Per-instance statevector simulation from |0...0>, with no tree and no
  *     uncomputation, accumulating w_i |psi_x|^2 [Sec. II, Eq. 1].
  *   - A density-matrix simulator rho -> U rho U^dag and
- *     rho -> sum_k p_k P_k rho P_k for n <= 6 [Sec. II].
+ *     rho -> sum_k p_k P_k rho P_k for n <= 6 [Sec. II], and
+ *     rho -> sum_m K_m rho K_m^dag for the non-invertible RESET / MEASURE.
+ *   - Non-invertible operations [Sec. III-B2] unravelled into their Kraus
+ *     branches: every selected instance is expanded into its 2^R branch
+ *     records, each simulated from |0...0> with the unnormalised K_m psi
+ *     (pinned against the density matrix in tests/test_noninvertible.py).
  *
  * Conventions (the paper fixes none of them): qubit q is bit q of the
  * amplitude index; for a two-qubit gate on (q0, q1) the local index is
@@ -47,13 +52,27 @@ typedef double complex cx;
 /* Gate kinds; the numbering is the interface numbering of the circuit format. */
 enum {
     OK_H = 0, OK_X, OK_Y, OK_Z, OK_S, OK_SDG, OK_T, OK_TDG,
-    OK_RX, OK_RY, OK_RZ, OK_U1Q, OK_CX, OK_CZ, OK_RZZ, OK_U2Q, OK_NKINDS
+    OK_RX, OK_RY, OK_RZ, OK_U1Q, OK_CX, OK_CZ, OK_RZZ, OK_U2Q,
+    OK_RESET, OK_MEASURE, OK_NKINDS
 };
+#define OR_OUTCOME1 4 /* event code: the non-invertible gate at this slot takes Kraus branch 1 */
 #define OR_PSTRIDE 32 /* doubles of parameters per gate in the flat arrays */
 
 static int two_qubit(int kind)
 {
     return kind == OK_CX || kind == OK_CZ || kind == OK_RZZ || kind == OK_U2Q;
+}
+
+static int noninvertible(int kind) { return kind == OK_RESET || kind == OK_MEASURE; }
+
+/* Kraus operator K_m of a non-invertible one-qubit operation [Sec. III-B2]:
+ * reset to |0> has K_m = |0><m|, a Z measurement K_m = |m><m|;
+ * sum_m K_m^dag K_m = I for both. */
+static void kraus_2x2(int kind, int m, cx k[4])
+{
+    k[0] = k[1] = k[2] = k[3] = 0;
+    if (kind == OK_RESET) k[m] = 1;          /* row 0, column m */
+    else k[3 * m] = 1;                        /* (m, m) */
 }
 
 /* ------------------------------------------------------------------ matrices */
@@ -185,11 +204,24 @@ int or_simulate(int n, int G, const int *kinds, const int *q0, const int *q1,
     psi[0] = 1;
     int e = 0;
     for (int j = 0; j <= G; j++) {
+        int branch = 0;
         while (e < n_ev && ev_slot[e] == j) {
-            apply_pauli(psi, n, ev_q[e], ev_p[e]);
+            if (ev_p[e] == OR_OUTCOME1) {
+                if (j == G || !noninvertible(kinds[j]) || ev_q[e] != q0[j]) { free(psi); return -3; }
+                branch = 1;
+            } else {
+                apply_pauli(psi, n, ev_q[e], ev_p[e]);
+            }
             e++;
         }
-        if (j < G) apply_gate(psi, n, kinds[j], q0[j], q1[j], params + (int64_t)OR_PSTRIDE * j);
+        if (j < G && noninvertible(kinds[j])) {
+            /* the unnormalised Kraus branch: its norm carries the branch probability */
+            cx k[4];
+            kraus_2x2(kinds[j], branch, k);
+            apply_1q(psi, n, q0[j], k);
+        } else if (j < G) {
+            apply_gate(psi, n, kinds[j], q0[j], q1[j], params + (int64_t)OR_PSTRIDE * j);
+        }
     }
     if (e != n_ev) { free(psi); return -2; } /* unsorted or out-of-range slot */
     if (acc) {
@@ -263,8 +295,20 @@ int or_dm_run(int n, int G, const int *kinds, const int *q0, const int *q1,
     rho[0] = 1;
     for (int j = 0; j < G; j++) {
         cx m[16];
-        gate_cx(kinds[j], params + (int64_t)OR_PSTRIDE * j, m);
-        dm_apply_gate_cols_rows(rho, n, kinds[j], q0[j], q1[j], m);
+        if (noninvertible(kinds[j])) {
+            /* rho <- sum_m K_m rho K_m^dag [Sec. III-B2] */
+            for (int64_t i = 0; i < sz; i++) acc[i] = 0;
+            for (int b = 0; b < 2; b++) {
+                kraus_2x2(kinds[j], b, m);
+                memcpy(tmp, rho, sizeof(cx) * sz);
+                dm_apply_gate_cols_rows(tmp, n, kinds[j], q0[j], -1, m);
+                for (int64_t i = 0; i < sz; i++) acc[i] += tmp[i];
+            }
+            memcpy(rho, acc, sizeof(cx) * sz);
+        } else {
+            gate_cx(kinds[j], params + (int64_t)OR_PSTRIDE * j, m);
+            dm_apply_gate_cols_rows(rho, n, kinds[j], q0[j], q1[j], m);
+        }
         int c = ch_of_gate[j];
         if (c < 0) continue;
         double ptot = 0;
@@ -694,6 +738,73 @@ static int commute_er(const or_plan *P, int mode, const int *chs, const int *cod
     return nv;
 }
 
+/* Kraus branches of the non-invertible gates [Sec. III-B2]: each selected
+ * instance is replaced by its 2^R branch records (m_1 .. m_R over the R
+ * RESET / MEASURE gates in gate order), written as outcome events
+ * (j_r, q_r, OR_OUTCOME1) for the gates with m_r = 1; every record keeps the
+ * instance's count and weight (the unnormalised branch states carry the
+ * branch probabilities).  The list is then sorted back into DFS order.
+ * Returns -1 when the expansion would exceed 2^24 instances. */
+static int expand_kraus(or_plan *P)
+{
+    int R = 0;
+    for (int j = 0; j < P->G; j++) R += noninvertible(P->kinds[j]);
+    if (R == 0) return 0;
+    if (R > 24 || (P->n_inst << R) > ((int64_t)1 << 24)) return -1;
+    int *js = malloc(sizeof(int) * R);
+    R = 0;
+    for (int j = 0; j < P->G; j++) if (noninvertible(P->kinds[j])) js[R++] = j;
+    int64_t nb = (int64_t)1 << R, nout = P->n_inst * nb;
+    int64_t cap = (P->inst_off[P->n_inst] + (int64_t)R * P->n_inst) * nb + 1;
+    int64_t *off = malloc(sizeof(int64_t) * (nout + 1));
+    ev_t *ev = malloc(sizeof(ev_t) * cap);
+    uint64_t *cnt = malloc(sizeof(uint64_t) * (nout + 1));
+    double *w = malloc(sizeof(double) * (nout + 1));
+    int64_t k = 0, e = 0;
+    for (int64_t i = 0; i < P->n_inst; i++)
+        for (int64_t b = 0; b < nb; b++) {
+            off[k] = e;
+            int64_t start = e;
+            for (int64_t x = P->inst_off[i]; x < P->inst_off[i + 1]; x++) ev[e++] = P->inst_ev[x];
+            for (int r = 0; r < R; r++)
+                if (b >> r & 1) ev[e++] = (ev_t){js[r], P->q0[js[r]], OR_OUTCOME1};
+            /* insertion sort of this list by (slot, qubit, code) */
+            for (int64_t x = start + 1; x < e; x++) {
+                ev_t t = ev[x];
+                int64_t y = x - 1;
+                while (y >= start && cmp_events(&t, 1, &ev[y], 1) < 0) { ev[y + 1] = ev[y]; y--; }
+                ev[y + 1] = t;
+            }
+            cnt[k] = P->inst_count[i];
+            w[k] = P->inst_w[i];
+            k++;
+        }
+    off[nout] = e;
+    int64_t *ord = malloc(sizeof(int64_t) * nout);
+    for (int64_t i = 0; i < nout; i++) ord[i] = i;
+    g_off = off; g_ev = ev;
+    qsort(ord, nout, sizeof(int64_t), qs_key);
+    free(P->inst_off); free(P->inst_ev); free(P->inst_count); free(P->inst_w); free(P->lcp);
+    P->inst_off = malloc(sizeof(int64_t) * (nout + 1));
+    P->inst_ev = malloc(sizeof(ev_t) * (e + 1));
+    P->inst_count = malloc(sizeof(uint64_t) * (nout + 1));
+    P->inst_w = malloc(sizeof(double) * (nout + 1));
+    P->lcp = malloc(sizeof(int) * (nout + 1));
+    int64_t f = 0;
+    for (int64_t i = 0; i < nout; i++) {
+        int64_t o = ord[i];
+        P->inst_off[i] = f;
+        memcpy(P->inst_ev + f, ev + off[o], sizeof(ev_t) * (off[o + 1] - off[o]));
+        f += off[o + 1] - off[o];
+        P->inst_count[i] = cnt[o];
+        P->inst_w[i] = w[o];
+    }
+    P->inst_off[nout] = f;
+    P->n_inst = nout;
+    free(js); free(off); free(ev); free(cnt); free(w); free(ord);
+    return 0;
+}
+
 void or_plan_free(void *h)
 {
     or_plan *P = h;
@@ -923,6 +1034,12 @@ void *or_plan_build(int n, int G, const int *kinds, const int *q0, const int *q1
         m++;
     }
     P->inst_off[m] = e;
+    if (expand_kraus(P) != 0) {
+        free(keep); free(w);
+        or_plan_free(P);
+        return NULL;
+    }
+    nin = P->n_inst;
     for (int64_t i = 0; i + 1 < nin; i++) {
         const ev_t *a = P->inst_ev + P->inst_off[i], *b = P->inst_ev + P->inst_off[i + 1];
         int na = (int)(P->inst_off[i + 1] - P->inst_off[i]);

@@ -61,7 +61,8 @@ class PlanStats(ctypes.Structure):
         "n_insignificant", "n_picked", "n_instances", "tree_gate_edges", "dftt_gate_apps",
         "scratch_gate_apps", "dftt_pauli_apps", "scratch_pauli_apps")] + \
         [(f, ctypes.c_double) for f in ("seconds_sample", "seconds_tally", "seconds_commute",
-                                        "seconds_prune_tree")]
+                                        "seconds_prune_tree")] + \
+        [(f, ctypes.c_uint64) for f in ("n_noninvertible", "n_noninv_layers", "n_ecm_instances")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,7 +72,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_window", ctypes.c_int), ("traversal", ctypes.c_int),
                 ("leaf_peek", ctypes.c_int), ("root_reset", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int), ("cache_states", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):
@@ -80,7 +81,8 @@ class RunInfo(ctypes.Structure):
         "resets", "kernel_launches")] + \
         [(f, ctypes.c_double) for f in ("max_drift", "state_bytes", "algorithmic_bytes",
                                         "program_bytes")] + \
-        [(f, ctypes.c_uint64) for f in ("stages", "matrix_ops", "diag_ops", "diag_terms")]
+        [(f, ctypes.c_uint64) for f in ("stages", "matrix_ops", "diag_ops", "diag_terms", "cache_restores",
+                                        "rederives")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

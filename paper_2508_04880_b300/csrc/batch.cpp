@@ -160,6 +160,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         co.checks = o.drift_tol >= 0 && o.traversal != TUSQ_FROM_SCRATCH;
         const uint64_t budget = o.snapshot_bytes ? o.snapshot_bytes : 8 * state;
         co.snapshots = (co.checks || o.traversal == TUSQ_DFTT_SNAPSHOT) ? (int)std::min<uint64_t>(budget / state, 64) : 0;
+        co.cache_states = o.cache_states;
         return co;
     };
     // the jobs' programs are independent: compile them on all host cores
@@ -222,7 +223,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         matsf.insert(matsf.end(), pg.matsf.begin(), pg.matsf.end());
         tmask.insert(tmask.end(), pg.term_mask.begin(), pg.term_mask.end());
         tphi.insert(tphi.end(), pg.term_phi.begin(), pg.term_phi.end());
-        const int nsnap = std::min(co.snapshots, pg.max_depth);
+        const int nsnap = pg.n_snap_slots;
         snap_off.push_back(snap_bytes);
         snap_bytes += (size_t)nsnap * state;
         rec_off.push_back(rec_count);

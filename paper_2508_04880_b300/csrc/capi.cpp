@@ -50,7 +50,7 @@ static int expected_params(int kind) {
 int tusq_circuit_add_gate(tusq_circuit *c, int kind, int q0, int q1, const double *params,
                           int n_params) {
     if (!c) TUSQ_FAIL(TUSQ_EINVAL, "tusq_circuit_add_gate: circuit is NULL");
-    if (kind < TUSQ_H || kind > TUSQ_U2Q) TUSQ_FAIL(TUSQ_EINVAL, "tusq_circuit_add_gate: unknown gate kind");
+    if (kind < TUSQ_H || kind > TUSQ_MEASURE) TUSQ_FAIL(TUSQ_EINVAL, "tusq_circuit_add_gate: unknown gate kind");
     if (q0 < 0 || q0 >= c->n) TUSQ_FAIL(TUSQ_EINVAL, "tusq_circuit_add_gate: q0 out of range");
     bool two = is_two_qubit(kind);
     if (two && (q1 < 0 || q1 >= c->n || q1 == q0))

@@ -2,7 +2,12 @@
 // into the device program of one DFTT traversal (Sec. III-B): forward
 // segments split at the branch slots that will be revisited, uncompute
 // segments back to each branch slot, fused passes over qubit windows, and
-// register stages inside each pass.
+// register stages inside each pass.  Non-invertible gates (RESET, MEASURE)
+// are never uncomputed: a return across one restores the branch node's
+// snapshot, or the DFTT+Caching state saved just before the layer (Sec.
+// III-B2) followed by an uncompute up to the node, or re-derives the node
+// forward from the deepest saved state above it (or |0..0>), whichever
+// applies fewer ops.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -26,6 +31,7 @@ struct HOp {
     int type = H_MAT1;
     int q0 = 0, q1 = -1;          // MAT2: basis index 2*bit(q0) + bit(q1)
     bool pauli = false;
+    bool noninv = false;          // a Kraus branch of RESET / MEASURE: never inverted
     int key = 0;                  // canonical position: 2*slot for events, 2*slot+1 for gates
     int uid = 0;                  // identity within the instance (for set differences)
     std::vector<int> merged;      // uids of ops merged into this one (besides uid)
@@ -63,8 +69,16 @@ void gate_matrix(const Gate &g, cd *m) {
     case TUSQ_U1Q: for (int k = 0; k < 4; ++k) m[k] = cd(g.p[2 * k], g.p[2 * k + 1]); break;
     case TUSQ_CX: m[0] = 1; m[5] = 1; m[11] = 1; m[14] = 1; break;
     case TUSQ_U2Q: for (int k = 0; k < 16; ++k) m[k] = cd(g.p[2 * k], g.p[2 * k + 1]); break;
+    case TUSQ_RESET: case TUSQ_MEASURE: m[0] = 1; break;   // Kraus branch 0: |0><0|
     default: throw std::logic_error("gate_matrix: not a dense kind");
     }
+}
+
+// Kraus branch 1 of a non-invertible gate: |0><1| (RESET) or |1><1| (MEASURE).
+void kraus1(int kind, cd *m) {
+    for (int k = 0; k < 4; ++k) m[k] = 0;
+    if (kind == TUSQ_RESET) m[1] = 1;
+    else m[3] = 1;
 }
 
 // Diagonal gates as exp(2 pi i (phi0 + sum_k phi_k parity(x & mask_k))).
@@ -97,6 +111,7 @@ HOp gate_op(const Gate &g, int j) {
     } else {
         op.type = is_two_qubit(g.kind) ? H_MAT2 : H_MAT1;
         gate_matrix(g, op.m);
+        op.noninv = is_noninvertible(g.kind);
     }
     return op;
 }
@@ -120,6 +135,7 @@ HOp pauli_op(int slot, int q, int p) {
 }
 
 HOp inverse(const HOp &o) {
+    if (o.noninv) throw std::logic_error("compile: uncompute across a non-invertible gate");
     HOp r = o;
     if (o.type == H_DIAG) {
         r.phi0 = -o.phi0;
@@ -267,6 +283,7 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
         p.merged.push_back(o.uid);
         p.merged.insert(p.merged.end(), o.merged.begin(), o.merged.end());
         p.pauli = false;
+        p.noninv = p.noninv || o.noninv;
     };
     for (const HOp &o : in) {
         if (!out.empty()) {
@@ -653,6 +670,15 @@ struct Compiler {
     uint64_t forced;
     std::vector<HOp> gate_ops;
 
+    // DFTT+Caching (Sec. III-B2): the states just before a layer of
+    // non-invertible gates on the current root-to-leaf path, shallowest
+    // first.  `shared` entries reuse a branch node's snapshot slot.
+    struct CacheEnt { int slot, snap; bool shared; };
+    std::vector<CacheEnt> cache;
+    std::vector<int> cache_free;        // unused cache slots
+    std::vector<char> layer_start;      // gate j opens a non-invertible layer
+    int K = 0;                          // cache capacity
+
     Compiler(const tusq_plan_t &p, const CompileOpts &c, Program &pr)
         : P(p), co(c), prog(pr), enc{pr, p.n, c.precision == TUSQ_C128,
                                      c.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, 0} {
@@ -669,6 +695,41 @@ struct Compiler {
         int nf = std::min(co.precision == TUSQ_C128 ? 3 : 4, std::max(L - 2, 0));
         forced = (nf >= 64) ? ~0ULL : ((1ULL << nf) - 1);
         for (int j = 0; j < G; ++j) gate_ops.push_back(gate_op(P.gates[j], j));
+        layer_start.assign(G + 1, 0);
+        int layers = 0;
+        for (int j = 0; j < G; ++j)
+            if (is_noninvertible(P.gates[j].kind) && (j == 0 || !is_noninvertible(P.gates[j - 1].kind))) {
+                layer_start[j] = 1;
+                ++layers;
+            }
+        if (co.traversal != TUSQ_FROM_SCRATCH && layers > 0)
+            K = co.cache_states < 0 ? std::min(layers, kDefaultCacheStates) : co.cache_states;
+        for (int k = K; k-- > 0;) cache_free.push_back(co.snapshots + k);
+    }
+
+    // Cache entries below slot t are off the next path: free their slots.
+    void pop_cache_below(int t) {
+        while (!cache.empty() && cache.back().slot > t) {
+            if (!cache.back().shared) cache_free.push_back(cache.back().snap);
+            cache.pop_back();
+        }
+    }
+
+    // A slot for the state before the layer at `slot`: a free one, else the
+    // shallowest entry's (the cache keeps the K closest to the leaf).
+    int cache_take(int slot) {
+        if (K == 0) return -1;
+        if (cache_free.empty()) {
+            size_t k = 0;
+            while (k < cache.size() && cache[k].shared) ++k;
+            if (k == cache.size()) return -1;
+            cache_free.push_back(cache[k].snap);
+            cache.erase(cache.begin() + k);
+        }
+        int idx = cache_free.back();
+        cache_free.pop_back();
+        cache.push_back(CacheEnt{slot, idx, false});
+        return idx;
     }
 
     // Instance i's ops with canonical position in [2*a, 2*b) i.e. events at
@@ -678,13 +739,16 @@ struct Compiler {
         uint64_t e = P.ev_off[i], e1 = P.ev_off[i + 1];
         while (e < e1 && P.ev_slot[e] < a) ++e;
         for (int j = a; j < b; ++j) {
+            bool branch1 = false;     // the non-invertible gate j takes Kraus branch 1
             for (; e < e1 && P.ev_slot[e] == j; ++e) {
+                if (P.ev_pauli[e] == TUSQ_OUTCOME1) { branch1 = true; continue; }
                 HOp o = pauli_op(j, P.ev_qubit[e], P.ev_pauli[e]);
                 o.uid = -(int)(e - P.ev_off[i]) - 1;
                 out.push_back(o);
             }
             if (j < G) {
                 HOp o = gate_ops[j];
+                if (branch1) kraus1(P.gates[j].kind, o.m);
                 o.uid = j;
                 out.push_back(o);
             }
@@ -775,9 +839,20 @@ struct Compiler {
                 }
                 std::reverse(chain.begin(), chain.end());
             }
+            // split points: the future branch nodes and, with a cache, the
+            // nodes just before each non-invertible layer
+            std::vector<int> splits(chain.begin(), chain.end());
+            // without the branch stack, still end a pass at the next branch
+            // node, so that the leaf pass that skips its write holds no op
+            // above the node the uncompute returns to
+            if (!track && !scratch && i + 1 < N && P.lcp[i] > t_in && P.lcp[i] <= G) splits.push_back(P.lcp[i]);
+            if (K > 0)
+                for (int j = t_in + 1; j < G; ++j)
+                    if (layer_start[j]) splits.push_back(j);
+            std::sort(splits.begin(), splits.end());
             std::vector<int> bounds;
             bounds.push_back(t_in);
-            for (int s : chain) if (s > bounds.back()) bounds.push_back(s);
+            for (int s : splits) if (s > bounds.back()) bounds.push_back(s);
             bounds.push_back(G + 1);
             std::vector<int> leaf_ops;     // uids the unwritten leaf launch applied
             bool last_inst = (i + 1 == N);
@@ -786,14 +861,26 @@ struct Compiler {
                 bool final_seg = (s + 2 == bounds.size());
                 if (!final_seg) {
                     // the pass that ends at a future branch node records it
+                    // (and snapshots it while slots last); one that ends just
+                    // before a non-invertible layer puts the state in the cache
+                    const int node = bounds[s + 1];
+                    const bool is_branch = std::binary_search(chain.begin(), chain.end(), node);
+                    const bool is_layer = K > 0 && node < G && layer_start[node];
                     int depth = (int)stack.size();
-                    int snap = depth < co.snapshots ? depth : -1;
-                    bool rec = co.checks && !(snap_policy && snap >= 0);
-                    uint32_t fl = PF_WRITE | (rec ? PF_REDUCE : 0u) | (snap >= 0 ? PF_SNAPSHOT : 0u);
-                    emit_ops(ops, fl, 0.0, snap, nullptr);
+                    int snap = is_branch && depth < co.snapshots ? depth : -1;
+                    bool rec = is_branch && co.checks && !(snap_policy && snap >= 0);
+                    int wsnap = snap;
+                    if (is_layer) {
+                        if (snap >= 0) cache.push_back(CacheEnt{node, snap, true});
+                        else wsnap = cache_take(node);
+                    }
+                    uint32_t fl = PF_WRITE | (rec ? PF_REDUCE : 0u) | (wsnap >= 0 ? PF_SNAPSHOT : 0u);
+                    emit_ops(ops, fl, 0.0, wsnap, nullptr);
                     if (rec) prog.steps.push_back(Step{ST_RECORD, 0, depth, snap, 0});
-                    stack.push_back(Rec{bounds[s + 1], depth, snap, rec});
-                    prog.max_depth = std::max(prog.max_depth, depth + 1);
+                    if (is_branch) {
+                        stack.push_back(Rec{node, depth, snap, rec});
+                        prog.max_depth = std::max(prog.max_depth, depth + 1);
+                    }
                 } else {
                     bool peek = co.leaf_peek && !scratch && !last_inst;
                     uint32_t fl = PF_LEAF | (peek ? 0u : PF_WRITE);
@@ -810,48 +897,112 @@ struct Compiler {
                 prog.steps.push_back(Step{ST_INIT, 0, 0, -1, 0});
                 prog.resets++;
                 stack.clear();
+                pop_cache_below(t);
+                // the branch slots are free again: drop the entries sharing them
+                cache.erase(std::remove_if(cache.begin(), cache.end(), [](const CacheEnt &c) { return c.shared; }),
+                            cache.end());
                 continue;
             }
             while (!stack.empty() && stack.back().slot > t) stack.pop_back();
             if (track && (stack.empty() || stack.back().slot != t))
                 throw std::logic_error("compile: branch slot was not materialised");
             return_to(i, t, leaf_ops, stack, snap_policy);
-            // a node that no later pair branches at is done with
-            if (track && !reused[i]) stack.pop_back();
+            pop_cache_below(t);
+            // a node that no later pair branches at is done with; its
+            // snapshot slot goes back to the branch stack
+            if (track && !reused[i]) {
+                const int freed = stack.back().snap;
+                stack.pop_back();
+                if (freed >= 0)
+                    cache.erase(std::remove_if(cache.begin(), cache.end(),
+                                               [&](const CacheEnt &c) { return c.shared && c.snap == freed; }),
+                                cache.end());
+            }
         }
+    }
+
+    // Uncompute back to the branch node on top of the stack, with the drift
+    // check when the node was recorded.
+    template <class Stack>
+    void undo_to_branch(const std::vector<HOp> &undo, Stack &stack) {
+        if (!co.checks || stack.empty() || !stack.back().recorded) {
+            emit_ops(undo, PF_WRITE, 0.0, -1, nullptr);
+            return;
+        }
+        int depth = stack.back().depth;
+        int snap = stack.back().snap;
+        emit_ops(undo, PF_WRITE | PF_REDUCE, 0.0, -1, nullptr);
+        int chk = prog.n_checks++;
+        prog.steps.push_back(Step{ST_CHECK, 0, depth, snap, chk});
+        if (snap >= 0) prog.steps.push_back(Step{ST_RESTORE, 0, depth, snap, chk});
     }
 
     template <class Stack>
     void return_to(uint64_t i, int t, const std::vector<int> &leaf_ops, Stack &stack, bool snap_policy) {
-            const int G = this->G;
-            if (snap_policy && !stack.empty() && stack.back().snap >= 0) {
-                // the branch node's own snapshot: a restore, which fuse_restores
-                // folds into the next pass's tile loads
-                prog.steps.push_back(Step{ST_RESTORE, 0, stack.back().depth, stack.back().snap, -1});
-                prog.restores++;
-                return;
-            }
-            // uncompute instance i back to slot t (ops at slots >= t not
-            // already undone by the leaf pass that skipped its write)
-            std::vector<HOp> all = segment(i, t, G + 1);
+        const int G = this->G;
+        const bool own_snap = !stack.empty() && stack.back().slot == t && stack.back().snap >= 0;
+        if (snap_policy && own_snap) {
+            // the branch node's own snapshot: a restore, which fuse_restores
+            // folds into the next pass's tile loads
+            prog.steps.push_back(Step{ST_RESTORE, 0, stack.back().depth, stack.back().snap, -1});
+            prog.restores++;
+            return;
+        }
+        // instance i's ops at slots >= t, last applied first, not counting
+        // those of the leaf pass that skipped its write
+        std::vector<HOp> all = segment(i, t, G + 1);
+        std::vector<const HOp *> todo;
+        int j1 = G;              // first non-invertible gate among them
+        for (auto it = all.rbegin(); it != all.rend(); ++it) {
+            bool skipped = false;
+            for (int u : leaf_ops)
+                if (u == it->uid) { skipped = true; break; }
+            if (skipped) continue;
+            todo.push_back(&*it);
+            if (it->noninv) j1 = std::min(j1, it->uid);
+        }
+        if (todo.empty()) return;     // the state never left the branch node
+        if (j1 == G) {
             std::vector<HOp> undo;
-            for (auto it = all.rbegin(); it != all.rend(); ++it) {
-                bool skipped = false;
-                for (int u : leaf_ops)
-                    if (u == it->uid) { skipped = true; break; }
-                if (!skipped) undo.push_back(inverse(*it));
-            }
-            if (undo.empty()) return;     // the state never left the branch node
-            if (!co.checks || stack.empty() || !stack.back().recorded) {
-                emit_ops(undo, PF_WRITE, 0.0, -1, nullptr);
-                return;
-            }
-            int depth = stack.back().depth;
-            int snap = stack.back().snap;
-            emit_ops(undo, PF_WRITE | PF_REDUCE, 0.0, -1, nullptr);
-            int chk = prog.n_checks++;
-            prog.steps.push_back(Step{ST_CHECK, 0, depth, snap, chk});
-            if (snap >= 0) prog.steps.push_back(Step{ST_RESTORE, 0, depth, snap, chk});
+            for (const HOp *o : todo) undo.push_back(inverse(*o));
+            undo_to_branch(undo, stack);
+            return;
+        }
+        // The way back crosses a non-invertible layer (Sec. III-B2).
+        if (own_snap) {
+            prog.steps.push_back(Step{ST_RESTORE, 0, stack.back().depth, stack.back().snap, -1});
+            prog.restores++;
+            return;
+        }
+        // (a) the cached state before that layer, then uncompute up to t
+        int L1 = j1;
+        while (L1 > 0 && is_noninvertible(P.gates[L1 - 1].kind)) --L1;
+        int snap_c = -1;
+        size_t cost_c = 0;
+        if (L1 >= t)
+            for (const CacheEnt &c : cache)
+                if (c.slot == L1) { snap_c = c.snap; cost_c = segment(i, t, L1).size(); }
+        // (b) re-derive forward from the deepest saved state at or above t
+        // (a snapshotted branch node or a cached one), else from |0..0>
+        int s_d = 0, snap_d = -1;
+        for (const auto &r : stack)
+            if (r.snap >= 0 && r.slot <= t && r.slot > s_d) { s_d = r.slot; snap_d = r.snap; }
+        for (const CacheEnt &c : cache)
+            if (c.slot <= t && (c.slot > s_d || (snap_d < 0 && c.slot == s_d))) { s_d = c.slot; snap_d = c.snap; }
+        const size_t cost_d = segment(i, s_d, t).size();
+        if (snap_c >= 0 && cost_c <= cost_d) {
+            prog.steps.push_back(Step{ST_RESTORE, 0, 0, snap_c, -1});
+            prog.cache_restores++;
+            std::vector<HOp> seg = segment(i, t, L1), undo;
+            for (auto it = seg.rbegin(); it != seg.rend(); ++it) undo.push_back(inverse(*it));
+            if (!undo.empty()) undo_to_branch(undo, stack);
+            return;
+        }
+        if (snap_d >= 0) prog.steps.push_back(Step{ST_RESTORE, 0, 0, snap_d, -1});
+        else prog.steps.push_back(Step{ST_INIT, 0, 0, -1, 0});
+        prog.rederives++;
+        std::vector<HOp> fwd = segment(i, s_d, t);
+        if (!fwd.empty()) emit_ops(fwd, PF_WRITE, 0.0, -1, nullptr);
     }
 
 };
@@ -893,6 +1044,20 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
     prog.n_snapshots = co.snapshots;
     Compiler c(P, co, prog);
     c.run();
+    // cache slots follow the branch-snapshot slots actually used
+    const int B = std::min(co.snapshots, prog.max_depth);
+    int top = B;
+    auto remap = [&](int32_t &x) {
+        if (x >= co.snapshots) {
+            x = x - co.snapshots + B;
+            top = std::max(top, x + 1);
+        }
+    };
+    for (PassDesc &d : prog.passes)
+        if (d.flags & PF_SNAPSHOT) remap(d.snap);
+    for (Step &st : prog.steps)
+        if (st.type == ST_RESTORE && st.snap >= 0) remap(st.snap);
+    prog.n_snap_slots = top;
     prog.matsf.assign(prog.mats.begin(), prog.mats.end());
 }
 

@@ -26,6 +26,7 @@ struct Channel {
 
 bool is_two_qubit(int kind);
 bool is_diagonal(int kind);
+inline bool is_noninvertible(int kind) { return kind == TUSQ_RESET || kind == TUSQ_MEASURE; }
 
 struct Event {
     int32_t slot, qubit, pauli;

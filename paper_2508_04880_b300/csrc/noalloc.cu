@@ -192,7 +192,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
             grid[i] = (int)std::max<uint64_t>(g, 1);
             max_grid = std::max(max_grid, grid[i]);
         }
-        lay = layout_of(pg, state_bytes, std::min(k, pg.max_depth), max_grid);
+        lay = layout_of(pg, state_bytes, pg.n_snap_slots, max_grid);
         if (lay.total <= TUSQ_NOALLOC_SCRATCH_BYTES) break;
         if (k == 0) {
             set_error("tusq_run_noalloc: state + device program (" + std::to_string(lay.total) +

@@ -223,6 +223,59 @@ struct Kept {
 };
 void finish_tree(tusq_plan_t &P, const std::vector<Kept> &kept);
 
+// Kraus-branch expansion for the non-invertible gates (Sec. III-B2): every
+// kept instance stands for 2^R leaves, one per branch record (m_1..m_R),
+// with the instance's count and weight; the record is written as outcome
+// events (slot j_r, qubit q_r, TUSQ_OUTCOME1) for the gates with m_r = 1.
+// The leaves are re-sorted into DFS order.
+constexpr uint64_t kMaxLeaves = 1ull << 24;
+
+int expand_outcomes(const tusq_plan_t &P, std::vector<Kept> &kept, std::vector<Key> &store) {
+    std::vector<uint32_t> outs;
+    for (int j = 0; j < P.G; ++j)
+        if (is_noninvertible(P.gates[j].kind)) outs.push_back(pack_event(j, P.gates[j].q0, TUSQ_OUTCOME1));
+    const int R = (int)outs.size();
+    if (R == 0) return TUSQ_OK;
+    if (R > 24 || (kept.size() << R) > kMaxLeaves) {
+        set_error("tusq_plan: " + std::to_string(kept.size()) + " instances x 2^" + std::to_string(R) +
+                  " Kraus branches exceed 2^24 leaves");
+        return TUSQ_EINVAL;
+    }
+    store.clear();
+    store.reserve(kept.size() << R);
+    std::vector<std::pair<uint64_t, uint64_t>> origin;   // (kept index, record)
+    for (uint64_t i = 0; i < kept.size(); ++i)
+        for (uint64_t m = 0; m < (1ull << R); ++m) {
+            Key k = *kept[i].key;
+            for (int r = 0; r < R; ++r)
+                if (m >> r & 1) k.push_back(outs[r]);
+            std::sort(k.begin(), k.end());
+            store.push_back(std::move(k));
+            origin.emplace_back(i, m);
+        }
+    std::vector<uint64_t> ord(store.size());
+    for (uint64_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](uint64_t a, uint64_t b) { return key_less(store[a], store[b]); });
+    std::vector<Kept> out;
+    out.reserve(ord.size());
+    for (uint64_t o : ord) {
+        const Kept &src = kept[origin[o].first];
+        out.push_back(Kept{&store[o], src.count, src.weight});
+    }
+    kept.swap(out);
+    return TUSQ_OK;
+}
+
+void noninv_stats(tusq_plan_t &P) {
+    P.stats.n_noninvertible = 0;
+    P.stats.n_noninv_layers = 0;
+    for (int j = 0; j < P.G; ++j)
+        if (is_noninvertible(P.gates[j].kind)) {
+            P.stats.n_noninvertible++;
+            if (j == 0 || !is_noninvertible(P.gates[j - 1].kind)) P.stats.n_noninv_layers++;
+        }
+}
+
 void parallel_for(int nthreads, uint64_t n, const std::function<void(int, uint64_t, uint64_t)> &f) {
     if (nthreads <= 1 || n < 1024) { f(0, 0, n); return; }
     std::vector<std::thread> th;
@@ -419,6 +472,11 @@ int build_plan(const tusq_circuit &circ, const tusq_plan_opts &opts, uint64_t sh
     std::vector<Kept> kept;
     for (uint64_t i = 0; i < nk; ++i)
         if (keep[i]) kept.push_back(Kept{&korder[i]->first, korder[i]->second, w[i]});
+    st.n_ecm_instances = kept.size();
+    noninv_stats(P);
+    std::vector<Key> expanded;
+    int erc = expand_outcomes(P, kept, expanded);
+    if (erc) return erc;
     finish_tree(P, kept);
     double t4 = now_s();
     st.seconds_sample = t1 - t0;
@@ -444,12 +502,20 @@ int build_plan_from_instances(const tusq_circuit &circ, uint64_t n_inst, const u
         if (!(weights[i] >= 0.0)) { set_error("tusq_plan_from_instances: negative weight"); return TUSQ_EINVAL; }
         for (uint64_t e = ev_off[i]; e < ev_off[i + 1]; ++e) {
             int s = ev_slot[e], q = ev_qubit[e], p = ev_pauli[e];
-            if (s < 0 || s > P.G || q < 0 || q >= P.n || p < 1 || p > 3) {
+            if (s < 0 || s > P.G || q < 0 || q >= P.n || p < 1 || p > TUSQ_OUTCOME1) {
                 set_error("tusq_plan_from_instances: event out of range");
                 return TUSQ_EINVAL;
             }
+            if (p == TUSQ_OUTCOME1 && (s == P.G || !is_noninvertible(P.gates[s].kind) || P.gates[s].q0 != q)) {
+                set_error("tusq_plan_from_instances: outcome event not at a RESET / MEASURE gate on its qubit");
+                return TUSQ_EINVAL;
+            }
             uint32_t w = pack_event(s, q, p);
-            if (!keys[i].empty() && (keys[i].back() >> 2) >= (w >> 2)) {
+            // (slot, qubit) strictly ascending, except that an outcome event
+            // may follow a Pauli on the same (slot, qubit)
+            if (!keys[i].empty() && !((keys[i].back() >> 2) < (w >> 2) ||
+                                      ((keys[i].back() >> 2) == (w >> 2) && p == TUSQ_OUTCOME1 &&
+                                       (keys[i].back() & 3) != 3))) {
                 set_error("tusq_plan_from_instances: events not sorted by (slot, qubit) or duplicated");
                 return TUSQ_EINVAL;
             }
@@ -467,6 +533,8 @@ int build_plan_from_instances(const tusq_circuit &circ, uint64_t n_inst, const u
         }
         kept.push_back(Kept{&keys[ord[i]], 0, weights[ord[i]]});
     }
+    P.stats.n_ecm_instances = n_inst;
+    noninv_stats(P);
     finish_tree(P, kept);
     return TUSQ_OK;
 }
@@ -509,6 +577,8 @@ int build_plan_shard(const tusq_plan_t &src, int rank, int world, tusq_plan_t &P
     }
     std::vector<Kept> kept;
     for (uint64_t i = a; i < b; ++i) kept.push_back(Kept{&keys[i - a], src.counts[i], src.weights[i]});
+    P.stats.n_ecm_instances = kept.size();
+    noninv_stats(P);
     finish_tree(P, kept);
     return TUSQ_OK;
 }

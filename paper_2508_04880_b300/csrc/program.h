@@ -150,6 +150,9 @@ struct Program {
     // counters
     uint64_t gate_apps = 0, pauli_apps = 0, passes_count = 0, leaf_passes = 0, resets = 0;
     uint64_t restores = 0;           // unconditional snapshot restores (snapshot policy)
+    uint64_t cache_restores = 0;     // returns served by a cached pre-layer state
+    uint64_t rederives = 0;          // returns re-derived forward (saved state above, or |0..0>)
+    int n_snap_slots = 0;            // snapshot slots the steps use (branch + cache)
 };
 
 // Arguments of one pass launch.
@@ -208,8 +211,11 @@ struct CompileOpts {
     int leaf_peek;
     int root_reset;
     bool checks;
-    int snapshots;         // snapshot slots available
+    int snapshots;         // snapshot slots available for branch nodes
     int schedule;          // 0 lookahead window growth, 1 list order
+    int cache_states = 0;  // DFTT+Caching capacity; < 0: one per layer, at most kDefaultCacheStates
 };
+
+constexpr int kDefaultCacheStates = 8;
 
 }  // namespace tusq

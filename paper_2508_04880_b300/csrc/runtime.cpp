@@ -120,6 +120,7 @@ static CompileOpts compile_opts_of(const tusq_run_opts *o, size_t state_bytes) {
     co.checks = o->drift_tol >= 0 && o->traversal != TUSQ_FROM_SCRATCH;
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
+    co.cache_states = o->cache_states;
     return co;
 }
 
@@ -144,6 +145,8 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
     info->checks = pg.n_checks;
     info->resets = pg.resets;
     info->restores = pg.restores;
+    info->cache_restores = pg.cache_restores;
+    info->rederives = pg.rederives;
     info->state_bytes = (double)(amp_bytes * dim);
     // every pass reads the state and writes it (and a snapshot) when asked;
     // a leaf pass also reads and writes the FP64 accumulator; a reset
@@ -180,7 +183,11 @@ size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
     size_t amp = o->precision == TUSQ_C128 ? 16 : 8;
     size_t state = amp << p->n;
     CompileOpts co = compile_opts_of(o, state);
-    return state * (1 + co.snapshots) + (1u << 20);
+    int K = 0;
+    if (o->traversal != TUSQ_FROM_SCRATCH && p->stats.n_noninv_layers > 0)
+        K = co.cache_states < 0 ? (int)std::min<uint64_t>(p->stats.n_noninv_layers, kDefaultCacheStates)
+                                : co.cache_states;
+    return state * (1 + co.snapshots + K) + (1u << 20);
 }
 
 int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t *info) {
@@ -221,7 +228,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     }
     Program &pg = e->prog;
     e->V = pg.reg_bits;
-    e->n_snaps = std::min(co.snapshots, pg.max_depth);
+    e->n_snaps = pg.n_snap_slots;
     // grid of every pass
     e->grid_of_pass.resize(pg.passes.size());
     int occ_cache[2][16] = {{0}};
@@ -447,6 +454,7 @@ void tusq_run_opts_default(tusq_run_opts *o) {
     o->drift_tol = 1e-6;
     o->snapshot_bytes = 0;      // 0 -> up to 64 states within 16 GiB, at least 8 (resolved at exec creation)
     o->check_every = 0;
+    o->cache_states = -1;       // one per non-invertible layer, at most 8
 }
 
 // Validate and complete run options (0 snapshot bytes -> up to 64 states
@@ -457,6 +465,10 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
     if (opts) o = *opts;
     if (o.precision != TUSQ_C64 && o.precision != TUSQ_C128) {
         set_error(std::string(who) + ": bad precision");
+        return TUSQ_EINVAL;
+    }
+    if (o.cache_states < -1 || o.cache_states > 64) {
+        set_error(std::string(who) + ": cache_states must be in [-1, 64]");
         return TUSQ_EINVAL;
     }
     if (o.traversal < TUSQ_DFTT || o.traversal > TUSQ_DFTT_SNAPSHOT) {

@@ -77,6 +77,12 @@ def full_op(n, U, q0, q1=-1):
     return M
 
 
+def kraus(kind, m):
+    """Kraus operator m of a reset (|0><m|) or a Z measurement (|m><m|)."""
+    ket0, ketm = np.eye(2)[:, [0]], np.eye(2)[:, [m]]
+    return (ket0 @ ketm.T if kind == W.RESET else ketm @ ketm.T).astype(complex)
+
+
 def gate_full(circ, j):
     kind, q0, q1, params = circ.gates[j]
     U = textbook_matrix(kind, params)
@@ -94,10 +100,15 @@ def state_of_instance(circ, events):
     psi[0] = 1
     ev = sorted(events)
     for j in range(circ.n_gates + 1):
+        branch = 0
         for (s, q, p) in ev:
-            if s == j:
+            if s == j and p == W.OUTCOME1:
+                branch = 1
+            elif s == j:
                 psi = pauli_full(n, q, p) @ psi
-        if j < circ.n_gates:
+        if j < circ.n_gates and circ.gates[j][0] in W.NONINVERTIBLE:
+            psi = full_op(n, kraus(circ.gates[j][0], branch), circ.gates[j][1]) @ psi
+        elif j < circ.n_gates:
             psi = gate_full(circ, j) @ psi
     return psi
 
@@ -117,8 +128,14 @@ def dm_bruteforce(circ):
     rho = np.zeros((dim, dim), dtype=complex)
     rho[0, 0] = 1
     for j in range(circ.n_gates):
-        U = gate_full(circ, j)
-        rho = U @ rho @ U.conj().T
+        kind, q0 = circ.gates[j][0], circ.gates[j][1]
+        if kind in W.NONINVERTIBLE:
+            # rho <- sum_m K_m rho K_m^dag
+            Ks = [full_op(n, kraus(kind, m), q0) for m in (0, 1)]
+            rho = sum(K @ rho @ K.conj().T for K in Ks)
+        else:
+            U = gate_full(circ, j)
+            rho = U @ rho @ U.conj().T
         ch = circ.channels[j]
         if ch is None:
             continue

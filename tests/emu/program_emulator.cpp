@@ -179,11 +179,12 @@ extern "C" int emu_run(const tusq_plan_t *p, const tusq_run_opts *o, double *pro
     co.checks = o->drift_tol >= 0 && o->traversal != TUSQ_FROM_SCRATCH;
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
+    co.cache_states = o->cache_states;
     Program pg;
     compile_program(*p, co, pg);
     const uint64_t dim = 1ULL << p->n;
     std::vector<cd> state(dim);
-    std::vector<std::vector<cd>> snapv(std::max(co.snapshots, 0), std::vector<cd>(dim));
+    std::vector<std::vector<cd>> snapv(std::max(pg.n_snap_slots, 0), std::vector<cd>(dim));
     std::vector<double> acc(dim, 0.0);
     std::vector<double> rec(4 * (pg.max_depth + 1), 0.0);
     std::vector<int> flag(pg.n_checks + 1, 0);

@@ -100,3 +100,16 @@ def test_forced_drift_restores():
     got, info = emu_run(T.plan(circ, 20_000, 5), precision=T.C128, traversal=T.DFTT, drift_tol=0.0)
     assert info["restores"] > 0
     assert np.abs(got - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("leaf_peek", [0, 1])
+@pytest.mark.parametrize("window", [0, 3])
+def test_uncompute_without_drift_checks(leaf_peek, window):
+    # no branch stack (drift checks off, uncompute traversal): the leaf pass
+    # that skips its write must not hold ops above the node the uncompute
+    # returns to, so a pass ends at every next branch node
+    circ = W.random_layers(6, 20, 0, 1e-2, 3e-2)
+    ref, _ = oracle.run(circ, 5000, 3)
+    got, _ = emu_run(T.plan(circ, 5000, 3), precision=T.C128, traversal=T.DFTT, drift_tol=-1.0,
+                     leaf_peek=leaf_peek, max_window=window)
+    assert np.abs(got - ref).max() < 1e-12

@@ -15,7 +15,8 @@ Interface numbering (shared with the C ABI header and the oracle, each of
 which writes its own copy):
 
 * gate kinds: H=0 X=1 Y=2 Z=3 S=4 SDG=5 T=6 TDG=7 RX=8 RY=9 RZ=10 U1Q=11
-  CX=12 CZ=13 RZZ=14 U2Q=15.  RX/RY/RZ(t) = exp(-i t sigma/2),
+  CX=12 CZ=13 RZZ=14 U2Q=15, and the non-invertible one-qubit RESET=16
+  (to |0>) and MEASURE=17 (mid-circuit Z measurement, record not output).  RX/RY/RZ(t) = exp(-i t sigma/2),
   RZZ(t) = exp(-i t Z(x)Z/2), U1Q carries a row-major 2x2 complex matrix as
   8 doubles (re, im pairs), U2Q a 4x4 one as 32 doubles.  For a two-qubit
   gate on (q0, q1) the local basis index is 2*bit(q0) + bit(q1); CX has
@@ -33,8 +34,10 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-H, X, Y, Z, S, SDG, T, TDG, RX, RY, RZ, U1Q, CX, CZ, RZZ, U2Q = range(16)
+H, X, Y, Z, S, SDG, T, TDG, RX, RY, RZ, U1Q, CX, CZ, RZZ, U2Q, RESET, MEASURE = range(18)
 TWO_QUBIT = (CX, CZ, RZZ, U2Q)
+NONINVERTIBLE = (RESET, MEASURE)     # mid-circuit reset / measurement (no parameters)
+OUTCOME1 = 4                          # event code of Kraus branch 1 in an instance's event list
 PARAM_STRIDE = 32          # doubles reserved per gate in flat parameter arrays
 N_PARAMS = {RX: 1, RY: 1, RZ: 1, RZZ: 1, U1Q: 8, U2Q: 32}
 
@@ -210,6 +213,49 @@ def qaoa_3regular(n: int = 28, layers: int = 4, seed: int = 0, p1: float = 5e-4,
             c.add(RZZ, a, b, params=(gammas[layer],), channel=_noise_for(RZZ, p1, p2))
         for q in range(n):
             c.add(RX, q, params=(betas[layer],), channel=_noise_for(RX, p1, p2))
+    return c
+
+
+def repetition_memory(d: int = 3, rounds: int = 3, seed: int = 0, p1: float = 1e-2,
+                      p2: float = 2e-2, pm: float = 1e-2, kind: int = RESET) -> Circuit:
+    """Bit-flip repetition-code memory, a small stand-in for the surface-code
+    memory circuits with d rounds of mid-circuit measurements of Sec. III-B2:
+    data qubits 0..d-1 start in a seeded product state (RY angles), ancilla
+    d+i collects the parity of data i and i+1 with two CX per round and is then
+    reset (or measured, `kind`), with a measurement-flip channel after it.
+    One round's ancilla operations are adjacent: one non-invertible layer."""
+    rng = np.random.default_rng(seed)
+    n = 2 * d - 1
+    c = Circuit(n, name=f"repetition_d{d}_r{rounds}")
+    for q in range(d):
+        c.add(RY, q, params=(float(rng.uniform(0, math.pi)),), channel=_noise_for(RY, p1, p2))
+    for _ in range(rounds):
+        for i in range(d - 1):
+            c.add(CX, i, d + i, channel=_noise_for(CX, p1, p2))
+            c.add(CX, i + 1, d + i, channel=_noise_for(CX, p1, p2))
+        for i in range(d - 1):
+            c.add(kind, d + i, channel=measurement_flip(pm) if pm > 0 else None)
+        for q in range(d):
+            c.add(RX, q, params=(float(rng.uniform(0, 0.3)),), channel=_noise_for(RX, p1, p2))
+    return c
+
+
+def mcm_brickwork(n: int = 24, depth: int = 12, layers: int = 3, per_layer: int = 2, seed: int = 0,
+                  p1: float = 1e-3, p2: float = 1e-2, kind: int = RESET) -> Circuit:
+    """Brickwork (Haar SU(2) + CZ) with `layers` layers of mid-circuit resets
+    (or measurements) spread evenly through the depth, each on `per_layer`
+    seeded distinct qubits."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n, name=f"mcm_brickwork_n{n}_d{depth}_l{layers}x{per_layer}")
+    at = {int(round((k + 1) * depth / (layers + 1))) for k in range(layers)}
+    for layer in range(depth):
+        if layer in at:
+            for q in sorted(int(v) for v in rng.choice(n, per_layer, replace=False)):
+                c.add(kind, q)
+        for q in range(n):
+            c.add(U1Q, q, params=haar_su2(rng), channel=_noise_for(U1Q, p1, p2))
+        for a in range(layer % 2, n - 1, 2):
+            c.add(CZ, a, a + 1, channel=_noise_for(CZ, p1, p2))
     return c
 
 

@@ -94,12 +94,14 @@ def test_batch_matches_oracle(traversal):
         close(o.cpu().numpy(), ref, T.C128, c.name)
 
 
-@pytest.mark.parametrize("precision", [T.C128, T.C64])
 @pytest.mark.parametrize("window", [0, 4])
-def test_uncompute_without_drift_checks(precision, window):
-    # a plain circuit: the leaf pass that skips its write, with no branch stack
+def test_uncompute_without_drift_checks(window):
+    # a plain circuit: the leaf pass that skips its write, with no branch
+    # stack.  Complex128 only: in complex64 the thousands of unchecked
+    # uncompute passes lose ~0.1% of the norm (measured: TV 1.2e-3 on this
+    # circuit), which is what the drift checks are there to catch
     c = W.random_layers(8, 20, 0, 1e-2, 3e-2)
     ref, _ = oracle.run(c, 10_000, 3)
-    got, _ = gpu_run(T.plan(c, 10_000, 3), precision=precision, traversal=T.DFTT, drift_tol=-1.0,
+    got, _ = gpu_run(T.plan(c, 10_000, 3), precision=T.C128, traversal=T.DFTT, drift_tol=-1.0,
                      max_window=window)
-    close(got, ref, precision)
+    close(got, ref, T.C128)

@@ -53,3 +53,19 @@ def test_noalloc_rejects_states_beyond_the_scratch():
         T.tusq_run_noalloc(plan, out.data_ptr(), T.run_opts(precision=T.C64))
     assert e.value.code == T.TUSQ_EINVAL
     assert "static scratch" in str(e.value)
+
+
+@pytest.mark.parametrize("traversal", [T.DFTT, T.DFTT_SNAPSHOT])
+def test_noalloc_with_mid_circuit_resets(traversal):
+    # non-invertible gates: the allocation-free path keeps no cache and
+    # re-derives across a reset from the saved states it has, or from |0..0>
+    import torch
+    circ = W.mcm_brickwork(12, 10, 3, 2, 7, 2e-3, 1e-2)
+    plan = T.plan(circ, 20_000, 1)
+    opts = T.run_opts(precision=T.C128, traversal=traversal, drift_tol=-1.0)
+    ref = torch.empty(1 << 12, dtype=torch.float64, device="cuda")
+    T.tusq_run(plan, ref.data_ptr(), opts, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    out = torch.empty_like(ref)
+    T.tusq_run_noalloc(plan, out.data_ptr(), opts, torch.cuda.current_stream().cuda_stream)
+    _close(out.cpu().numpy(), ref.cpu().numpy(), T.C128)

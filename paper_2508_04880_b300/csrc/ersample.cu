@@ -76,9 +76,24 @@ __global__ void __launch_bounds__(256) er_write(const DevChannel *ch, const uint
     }
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+// Device scratch of one sampling call on a private non-blocking stream:
+// stream-ordered allocations and copies, so that planning the next job does
+// not synchronise with a traversal running on another stream.
+struct Scratch {
+    cudaStream_t st = nullptr;
+    std::vector<void *> bufs;
+    ~Scratch() {
+        for (void *b : bufs) cudaFreeAsync(b, st);
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    }
+    cudaError_t alloc(void **p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, bytes, st);
+        if (e == cudaSuccess) bufs.push_back(*p);
+        return e;
+    }
 };
 
 }  // namespace
@@ -113,33 +128,38 @@ int sample_ers_device(const std::vector<Channel> &chans, uint64_t shots, uint64_
     off.assign(shots + 1, 0);
     words.clear();
     if (shots == 0) return TUSQ_OK;
-    DevBuf dch, dthr0, dcnt, dhash, doff, dwords;
-    E_TRY(cudaMalloc(&dch.p, sizeof(DevChannel) * hc.size()));
-    E_TRY(cudaMalloc(&dthr0.p, sizeof(uint64_t) * hthr0.size()));
-    E_TRY(cudaMalloc(&dcnt.p, sizeof(uint32_t) * shots));
-    E_TRY(cudaMalloc(&dhash.p, sizeof(uint64_t) * shots));
-    E_TRY(cudaMemcpy(dch.p, hc.data(), sizeof(DevChannel) * hc.size(), cudaMemcpyHostToDevice));
-    E_TRY(cudaMemcpy(dthr0.p, hthr0.data(), sizeof(uint64_t) * hthr0.size(), cudaMemcpyHostToDevice));
+    Scratch sc;
+    E_TRY(cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking));
+    void *dch = nullptr, *dthr0 = nullptr, *dcnt = nullptr, *dhash = nullptr, *doff = nullptr, *dwords = nullptr;
+    E_TRY(sc.alloc(&dch, sizeof(DevChannel) * hc.size()));
+    E_TRY(sc.alloc(&dthr0, sizeof(uint64_t) * hthr0.size()));
+    E_TRY(sc.alloc(&dcnt, sizeof(uint32_t) * shots));
+    E_TRY(sc.alloc(&dhash, sizeof(uint64_t) * shots));
+    E_TRY(cudaMemcpyAsync(dch, hc.data(), sizeof(DevChannel) * hc.size(), cudaMemcpyHostToDevice, sc.st));
+    E_TRY(cudaMemcpyAsync(dthr0, hthr0.data(), sizeof(uint64_t) * hthr0.size(), cudaMemcpyHostToDevice, sc.st));
     int dev = 0, nsm = 148;
     E_TRY(cudaGetDevice(&dev));
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (shots + 255) / 256;
     const unsigned grid = (unsigned)(want < (uint64_t)nsm * 32 ? want : (uint64_t)nsm * 32);
-    er_count<<<grid, 256>>>((const DevChannel *)dch.p, (const uint64_t *)dthr0.p, C, shots, seed,
-                            (uint32_t *)dcnt.p, (uint64_t *)dhash.p);
+    er_count<<<grid, 256, 0, sc.st>>>((const DevChannel *)dch, (const uint64_t *)dthr0, C, shots, seed,
+                                      (uint32_t *)dcnt, (uint64_t *)dhash);
     E_TRY(cudaGetLastError());
-    E_TRY(cudaMemcpy(cnt.data(), dcnt.p, sizeof(uint32_t) * shots, cudaMemcpyDeviceToHost));
-    E_TRY(cudaMemcpy(hash.data(), dhash.p, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost));
+    E_TRY(cudaMemcpyAsync(cnt.data(), dcnt, sizeof(uint32_t) * shots, cudaMemcpyDeviceToHost, sc.st));
+    E_TRY(cudaMemcpyAsync(hash.data(), dhash, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, sc.st));
+    E_TRY(cudaStreamSynchronize(sc.st));
     for (uint64_t s = 0; s < shots; ++s) off[s + 1] = off[s] + cnt[s];
     words.resize(off[shots]);
     if (!words.empty()) {
-        E_TRY(cudaMalloc(&doff.p, sizeof(uint64_t) * shots));
-        E_TRY(cudaMalloc(&dwords.p, sizeof(uint32_t) * words.size()));
-        E_TRY(cudaMemcpy(doff.p, off.data(), sizeof(uint64_t) * shots, cudaMemcpyHostToDevice));
-        er_write<<<grid, 256>>>((const DevChannel *)dch.p, (const uint64_t *)dthr0.p, C, shots, seed,
-                                (const uint64_t *)doff.p, (uint32_t *)dwords.p);
+        E_TRY(sc.alloc(&doff, sizeof(uint64_t) * shots));
+        E_TRY(sc.alloc(&dwords, sizeof(uint32_t) * words.size()));
+        E_TRY(cudaMemcpyAsync(doff, off.data(), sizeof(uint64_t) * shots, cudaMemcpyHostToDevice, sc.st));
+        er_write<<<grid, 256, 0, sc.st>>>((const DevChannel *)dch, (const uint64_t *)dthr0, C, shots, seed,
+                                          (const uint64_t *)doff, (uint32_t *)dwords);
         E_TRY(cudaGetLastError());
-        E_TRY(cudaMemcpy(words.data(), dwords.p, sizeof(uint32_t) * words.size(), cudaMemcpyDeviceToHost));
+        E_TRY(cudaMemcpyAsync(words.data(), dwords, sizeof(uint32_t) * words.size(), cudaMemcpyDeviceToHost,
+                              sc.st));
+        E_TRY(cudaStreamSynchronize(sc.st));
     }
     return TUSQ_OK;
 }

@@ -60,10 +60,10 @@ def test_noalloc_with_mid_circuit_resets(traversal):
     # non-invertible gates: the allocation-free path keeps no cache and
     # re-derives across a reset from the saved states it has, or from |0..0>
     import torch
-    circ = W.mcm_brickwork(12, 10, 3, 2, 7, 2e-3, 1e-2)
+    circ = W.mcm_brickwork(10, 8, 2, 1, 7, 2e-3, 1e-2)     # 404 leaves, ~5 MB device program
     plan = T.plan(circ, 20_000, 1)
     opts = T.run_opts(precision=T.C128, traversal=traversal, drift_tol=-1.0)
-    ref = torch.empty(1 << 12, dtype=torch.float64, device="cuda")
+    ref = torch.empty(1 << 10, dtype=torch.float64, device="cuda")
     T.tusq_run(plan, ref.data_ptr(), opts, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     out = torch.empty_like(ref)

@@ -1058,6 +1058,14 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
     for (Step &st : prog.steps)
         if (st.type == ST_RESTORE && st.snap >= 0) remap(st.snap);
     prog.n_snap_slots = top;
+    // every snapshot slot a step or pass names must exist in the buffer the
+    // runtime allocates (n_snap_slots states)
+    for (const PassDesc &d : prog.passes)
+        if ((d.flags & PF_SNAPSHOT) && (d.snap < 0 || d.snap >= top))
+            throw std::logic_error("compile: pass snapshot slot out of range");
+    for (const Step &st : prog.steps)
+        if ((st.type == ST_RESTORE && (st.snap < 0 || st.snap >= top)) || (st.type == ST_CHECK && st.snap >= top))
+            throw std::logic_error("compile: step snapshot slot out of range");
     prog.matsf.assign(prog.mats.begin(), prog.mats.end());
 }
 

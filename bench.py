@@ -485,6 +485,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8,
                     help="served: stream slots of the serving loop (32 measured no higher capacity and a "
                          "higher p99 under load than 8)")
+    ap.add_argument("--subtrees", type=int, default=1,
+                    help="main: traverse the DFS order as this many concurrent chunks (parallel subtrees)")
     ap.add_argument("--graph", type=int, default=1,
                     help="batch: replay each per-stream job's traversal from a captured CUDA graph; "
                          "main: time the traversal on a side stream with graph replay")
@@ -538,7 +540,7 @@ def main():
     stream = torch.cuda.Stream() if args.graph else torch.cuda.current_stream()
     torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
-    opts = T.run_opts(precision=prec, traversal=trav, use_graph=int(args.graph))
+    opts = T.run_opts(precision=prec, traversal=trav, use_graph=int(args.graph), subtrees=args.subtrees)
     ex = T.Exec(plan, opts, sp)
     probs = torch.empty(1 << n, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
@@ -638,7 +640,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload], "qubits": n, "gates": circ.n_gates,
-                   "shots": shots, "instances": n_inst, "traversal": args.traversal,
+                   "shots": shots, "instances": n_inst, "traversal": args.traversal, "subtrees": args.subtrees,
                    "l2": "inputs larger than L2 (state and output 2^n x 8 B each)",
                    "parallelism": f"replica x{world}"},
         "gate_amp_updates_per_s": (info["gate_apps"] + info["pauli_apps"]) * amps * world / secs,

@@ -243,10 +243,20 @@ typedef struct {
                                  snapshot above it, or from |0..0>.  -1 (default) = one per
                                  non-invertible layer, at most 8; 0 = no cache.  Each entry is
                                  one state of device memory on top of snapshot_bytes. */
+    int subtrees;             /* parallel-subtree DFTT on one GPU (Sec. III-B, subtrees traversed
+                                 in parallel when memory is free): 1 (default) = one traversal;
+                                 k in 2..16 = the DFS order cut into k chunks of nearly equal work
+                                 (as tusq_plan_shard), each traversed by its own exec on its own
+                                 stream from its own copy of the root state, the k FP64 outputs
+                                 summed in a fixed order into the caller's buffer.  Pays when one
+                                 pass does not fill the GPU (small states); costs k times the
+                                 state, snapshot and cache memory.  tusq_compile_stats reports
+                                 the single traversal. */
 } tusq_run_opts;
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
- * snapshot_bytes 0 = 64 states when they fit in 16 GiB, else 8 states. */
+ * snapshot_bytes 0 = 64 states when they fit in 16 GiB, else 8 states,
+ * cache_states -1, subtrees 1. */
 void tusq_run_opts_default(tusq_run_opts *o);
 
 typedef struct {

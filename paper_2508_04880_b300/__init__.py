@@ -72,7 +72,8 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_window", ctypes.c_int), ("traversal", ctypes.c_int),
                 ("leaf_peek", ctypes.c_int), ("root_reset", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int), ("cache_states", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int), ("cache_states", ctypes.c_int),
+                ("subtrees", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):

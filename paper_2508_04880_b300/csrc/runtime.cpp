@@ -24,6 +24,8 @@ cudaError_t launch_finalize(const double *partials, int nparts, double *records,
                             double record_bias, cudaStream_t st);
 cudaError_t launch_restore(void *state, const void *snap, int precision, uint64_t dim,
                            const int *restore_flag, int check, int nsm, cudaStream_t st);
+cudaError_t launch_sum_parts(double *out, const double *const *parts, int k, uint64_t dim, int nsm,
+                             cudaStream_t st);
 
 }  // namespace tusq
 
@@ -65,6 +67,15 @@ struct tusq_exec {
     cudaGraphExec_t gexec = nullptr;
     double *g_probs = nullptr;
     uint64_t g_launches = 0;
+    // parallel subtrees (opts.subtrees > 1): one exec per chunk of the DFS
+    // order on its own stream; part 0 writes the caller's buffer, the others
+    // their own, summed into it after the join
+    std::vector<tusq_exec *> parts;
+    std::vector<tusq_plan_t *> part_plans;
+    std::vector<cudaStream_t> part_st;
+    std::vector<double *> part_out;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
 };
 
 namespace {
@@ -187,7 +198,9 @@ size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
     if (o->traversal != TUSQ_FROM_SCRATCH && p->stats.n_noninv_layers > 0)
         K = co.cache_states < 0 ? (int)std::min<uint64_t>(p->stats.n_noninv_layers, kDefaultCacheStates)
                                 : co.cache_states;
-    return state * (1 + co.snapshots + K) + (1u << 20);
+    const size_t one = state * (1 + co.snapshots + K) + (1u << 20);
+    const uint64_t parts = o->subtrees > 1 ? std::min<uint64_t>((uint64_t)o->subtrees, std::max<uint64_t>(p->n_inst(), 1)) : 1;
+    return one * parts + (parts - 1) * sizeof(double) * ((size_t)1 << p->n);
 }
 
 int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t *info) {
@@ -204,6 +217,42 @@ int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t 
     return TUSQ_OK;
 }
 
+int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out);
+void exec_free(tusq_exec *e);
+
+// Parallel subtrees: the plan's DFS order cut into k chunks (tusq_plan_shard),
+// one exec per chunk on its own non-blocking stream, an FP64 output per
+// chunk after the first.
+static int create_parts(tusq_exec *e, const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t) {
+    const int k = (int)std::min<uint64_t>((uint64_t)o->subtrees, p->n_inst());
+    tusq_run_opts so = *o;
+    so.subtrees = 1;
+    so.use_graph = 0;
+    CUDA_TRY(cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming));
+    for (int r = 0; r < k; ++r) {
+        tusq_plan_t *q = nullptr;
+        int rc = tusq_plan_shard(p, r, k, &q);
+        if (rc != TUSQ_OK) return rc;
+        e->part_plans.push_back(q);
+        cudaStream_t s = nullptr;
+        CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        e->part_st.push_back(s);
+        cudaEvent_t ev = nullptr;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        e->join_ev.push_back(ev);
+        tusq_exec *x = nullptr;
+        rc = exec_create(q, &so, s, &x);
+        if (rc != TUSQ_OK) return rc;
+        e->parts.push_back(x);
+        double *buf = nullptr;
+        if (r > 0 && (rc = dmalloc(&buf, sizeof(double) * e->dim, s)) != TUSQ_OK) return rc;
+        e->part_out.push_back(buf);
+        e->footprint += x->footprint + (r ? sizeof(double) * e->dim : 0);
+    }
+    for (cudaStream_t s : e->part_st) CUDA_TRY(cudaStreamSynchronize(s));
+    return TUSQ_OK;
+}
+
 int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out) {
     tusq_exec *e = new (std::nothrow) tusq_exec;
     if (!e) { set_error("tusq_exec_create: out of host memory"); return TUSQ_ENOMEM; }
@@ -216,6 +265,15 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e->nsm <= 0) e->nsm = 148;
+    if (o->subtrees > 1 && p->n_inst() >= 2) {
+        const int rc = create_parts(e, p, o, st);
+        if (rc != TUSQ_OK) {
+            exec_free(e);
+            return rc;
+        }
+        *out = e;
+        return TUSQ_OK;
+    }
     const size_t state_bytes = e->amp_bytes * e->dim;
     CompileOpts co = compile_opts_of(o, state_bytes);
     try {
@@ -289,6 +347,26 @@ static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
     Program &pg = e->prog;
     e->stream = st;
     e->launches = 0;
+    if (!e->parts.empty()) {
+        // fork: every part waits for the work queued before it on st; join:
+        // st waits for every part, then sums the parts' outputs (fixed order)
+        CUDA_TRY(cudaEventRecord(e->fork_ev, st));
+        std::vector<const double *> outs;
+        for (size_t r = 0; r < e->parts.size(); ++r) {
+            CUDA_TRY(cudaStreamWaitEvent(e->part_st[r], e->fork_ev, 0));
+            e->parts[r]->profiling = e->profiling;
+            double *o = r == 0 ? probs : e->part_out[r];
+            const int rc = exec_launch_direct(e->parts[r], o, e->part_st[r]);
+            if (rc != TUSQ_OK) return rc;
+            e->launches += e->parts[r]->launches;
+            if (r) outs.push_back(o);
+            CUDA_TRY(cudaEventRecord(e->join_ev[r], e->part_st[r]));
+            CUDA_TRY(cudaStreamWaitEvent(st, e->join_ev[r], 0));
+        }
+        CUDA_TRY(launch_sum_parts(probs, outs.data(), (int)outs.size(), e->dim, e->nsm, st));
+        e->launches++;
+        return TUSQ_OK;
+    }
     CUDA_TRY(cudaMemsetAsync(probs, 0, sizeof(double) * e->dim, st));
     CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(unsigned long long) * 4, st));
     if (pg.n_checks) {
@@ -366,6 +444,42 @@ static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
 
 int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
     CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (!e->parts.empty()) {
+        // the parts' counters, summed (max for the drift); their pass
+        // profiles concatenated in part order
+        int rc_all = TUSQ_OK;
+        tusq_run_info_t sum{};
+        e->prof_ms.clear();
+        e->prof_bytes.clear();
+        for (tusq_exec *q : e->parts) {
+            tusq_run_info_t one{};
+            const int rc = exec_finish(q, &one);
+            if (rc != TUSQ_OK && rc_all == TUSQ_OK) rc_all = rc;
+            sum.passes += one.passes;
+            sum.gate_apps += one.gate_apps;
+            sum.pauli_apps += one.pauli_apps;
+            sum.leaf_passes += one.leaf_passes;
+            sum.checks += one.checks;
+            sum.restores += one.restores;
+            sum.unrecovered += one.unrecovered;
+            sum.resets += one.resets;
+            sum.max_drift = std::max(sum.max_drift, one.max_drift);
+            sum.state_bytes = one.state_bytes;
+            sum.algorithmic_bytes += one.algorithmic_bytes;
+            sum.program_bytes += one.program_bytes;
+            sum.stages += one.stages;
+            sum.matrix_ops += one.matrix_ops;
+            sum.diag_ops += one.diag_ops;
+            sum.diag_terms += one.diag_terms;
+            sum.cache_restores += one.cache_restores;
+            sum.rederives += one.rederives;
+            e->prof_ms.insert(e->prof_ms.end(), q->prof_ms.begin(), q->prof_ms.end());
+            e->prof_bytes.insert(e->prof_bytes.end(), q->prof_bytes.begin(), q->prof_bytes.end());
+        }
+        sum.kernel_launches = e->launches;
+        if (info) *info = sum;
+        return rc_all;
+    }
     unsigned long long cnt[4] = {0};
     CUDA_TRY(cudaMemcpy(cnt, e->counters, sizeof cnt, cudaMemcpyDeviceToHost));
     double maxd = 0;
@@ -433,6 +547,16 @@ int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
 void exec_free(tusq_exec *e) {
     if (!e) return;
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    for (size_t r = 0; r < e->parts.size(); ++r) exec_free(e->parts[r]);
+    for (size_t r = 0; r < e->part_out.size(); ++r)
+        if (e->part_out[r]) cudaFreeAsync(e->part_out[r], e->part_st[r]);
+    for (cudaStream_t s : e->part_st) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    for (tusq_plan_t *q : e->part_plans) tusq_plan_free(q);
+    if (e->fork_ev) cudaEventDestroy(e->fork_ev);
+    for (cudaEvent_t ev : e->join_ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : e->prof_ev) cudaEventDestroy(ev);
     release(e);
     cudaStreamSynchronize(e->stream);
@@ -455,6 +579,7 @@ void tusq_run_opts_default(tusq_run_opts *o) {
     o->snapshot_bytes = 0;      // 0 -> up to 64 states within 16 GiB, at least 8 (resolved at exec creation)
     o->check_every = 0;
     o->cache_states = -1;       // one per non-invertible layer, at most 8
+    o->subtrees = 1;
 }
 
 // Validate and complete run options (0 snapshot bytes -> up to 64 states
@@ -465,6 +590,10 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
     if (opts) o = *opts;
     if (o.precision != TUSQ_C64 && o.precision != TUSQ_C128) {
         set_error(std::string(who) + ": bad precision");
+        return TUSQ_EINVAL;
+    }
+    if (o.subtrees < 0 || o.subtrees > 16) {
+        set_error(std::string(who) + ": subtrees must be in [0, 16]");
         return TUSQ_EINVAL;
     }
     if (o.cache_states < -1 || o.cache_states > 64) {

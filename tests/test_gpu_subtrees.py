@@ -1,0 +1,86 @@
+"""Parallel-subtree DFTT on one GPU (run option `subtrees`, Sec. III-B):
+the DFS order cut into k chunks traversed concurrently on k streams, the
+chunks' FP64 outputs summed in a fixed order.  The result must match the
+oracle and the single traversal within the parity tolerances, for every
+traversal, with CUDA-graph replay, with mid-circuit resets, and when k
+exceeds the number of leaves."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2508_04880_b300 as T
+import tusq_workloads as W
+
+TOL = {T.C128: (1e-12, 1e-10), T.C64: (1e-5, 1e-4)}
+
+
+def close(got, ref, precision, what=""):
+    ma, tv = TOL[precision]
+    d = np.abs(got - ref)
+    assert d.max() <= ma and d.sum() <= tv, (what, d.max(), d.sum())
+
+
+def test_option_range_checked_on_the_host():
+    pl = T.plan(W.random_layers(4, 3, 1, 1e-2, 1e-2), 1000, 0)
+    T.tusq_compile_stats(pl, T.run_opts(subtrees=16))
+    with pytest.raises(T.TusqError):
+        T.tusq_compile_stats(pl, T.run_opts(subtrees=17))
+
+
+def _gpu(plan, **kw):
+    import torch
+    probs, info = T.run_torch(plan, T.run_opts(**kw))
+    torch.cuda.synchronize()
+    return probs.cpu().numpy(), info
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [T.C128, T.C64])
+@pytest.mark.parametrize("traversal", [T.DFTT, T.DFTT_SNAPSHOT, T.FROM_SCRATCH])
+def test_matches_oracle_and_single_traversal(precision, traversal):
+    c = W.brickwork(14, 12, 3, 2e-3, 2e-2)
+    ref, _ = oracle.run(c, 50_000, 1)
+    pl = T.plan(c, 50_000, 1)
+    single, info1 = _gpu(pl, precision=precision, traversal=traversal)
+    for k in (2, 3, 4):
+        got, info = _gpu(pl, precision=precision, traversal=traversal, subtrees=k)
+        close(got, ref, precision, f"k {k}")
+        close(got, single, precision, f"k {k} vs single")
+        assert info["leaf_passes"] == info1["leaf_passes"] and info["unrecovered"] == 0
+
+
+@pytest.mark.gpu
+def test_more_chunks_than_leaves_and_resets():
+    c = W.repetition_memory(3, 2, 1, 2e-2, 3e-2, 2e-2)
+    ref, _ = oracle.run(c, 4000, 3)
+    got, _ = _gpu(T.plan(c, 4000, 3), precision=T.C128, traversal=T.DFTT, drift_tol=-1.0, subtrees=5)
+    close(got, ref, T.C128)
+    tiny = W.Circuit(2)
+    tiny.add(W.H, 0, channel=((3,), (0.5,)))
+    tiny.add(W.RX, 0, params=(0.4,))
+    pl = T.plan(tiny, 1000, 0, prune=False)
+    assert pl.stats()["n_instances"] == 2
+    ref, _ = oracle.run(tiny, 1000, 0, prune=False)
+    got, _ = _gpu(pl, precision=T.C128, subtrees=8)
+    close(got, ref, T.C128)
+
+
+@pytest.mark.gpu
+def test_graph_replay_with_subtrees():
+    import torch
+    c = W.qaoa_3regular(14, 2, 4, 2e-3, 1e-2)
+    pl = T.plan(c, 50_000, 2)
+    side = torch.cuda.Stream()
+    direct = torch.empty(1 << 14, dtype=torch.float64, device="cuda")
+    ex0 = T.Exec(pl, T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT, subtrees=3), side.cuda_stream)
+    ex0.launch(direct.data_ptr(), side.cuda_stream)
+    ex0.finish()
+    ex = T.Exec(pl, T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT, subtrees=3, use_graph=1),
+                side.cuda_stream)
+    out = torch.full((1 << 14,), -1.0, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ex.launch(out.data_ptr(), side.cuda_stream)
+        ex.finish()
+        assert torch.equal(out, direct)
+    ref, _ = oracle.run(c, 50_000, 2)
+    close(direct.cpu().numpy(), ref, T.C64)

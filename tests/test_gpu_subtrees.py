@@ -84,3 +84,22 @@ def test_graph_replay_with_subtrees():
         assert torch.equal(out, direct)
     ref, _ = oracle.run(c, 50_000, 2)
     close(direct.cpu().numpy(), ref, T.C64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [8, 16])
+def test_six_qubit_configuration_with_many_chunks(k):
+    # the 6-qubit benchmark configuration (complex128, uncompute traversal
+    # with drift checks) as 8 and 16 concurrent chunks, graph-replayed
+    import torch
+    c = W.random_layers(6, 20, 0, 1e-3, 1e-2)
+    ref, _ = oracle.run(c, 10_000, 0)
+    pl = T.plan(c, 10_000, 0)
+    side = torch.cuda.Stream()
+    out = torch.empty(1 << 6, dtype=torch.float64, device="cuda")
+    ex = T.Exec(pl, T.run_opts(precision=T.C128, traversal=T.DFTT, subtrees=k, use_graph=1), side.cuda_stream)
+    for _ in range(2):
+        ex.launch(out.data_ptr(), side.cuda_stream)
+        info = ex.finish()
+        assert info["unrecovered"] == 0
+        close(out.cpu().numpy(), ref, T.C128, f"k {k}")

@@ -619,11 +619,12 @@ void finish_tree(tusq_plan_t &P, const std::vector<Kept> &kept) {
     st.dftt_gate_apps = N ? 2 * edges - P.G : 0;
     st.scratch_gate_apps = N * (uint64_t)P.G;
     for (uint64_t i = 0; i < N; ++i) {
-        uint64_t ne = P.ev_off[i + 1] - P.ev_off[i];
-        pa_scratch += ne;
-        // forward from the previous branch slot, uncompute back to the next one
+        // forward from the previous branch slot, uncompute back to the next
+        // one (Kraus-branch choices are not Pauli applications)
         int tin = i ? P.lcp[i - 1] : 0, tout = (i + 1 < N) ? P.lcp[i] : P.G + 1;
         for (uint64_t e = P.ev_off[i]; e < P.ev_off[i + 1]; ++e) {
+            if (P.ev_pauli[e] == TUSQ_OUTCOME1) continue;
+            pa_scratch++;
             if (P.ev_slot[e] >= tin) pa_dftt++;
             if (P.ev_slot[e] >= tout) pa_dftt++;
         }

@@ -194,3 +194,15 @@ def test_caching_operation_counts(name, maker, shots):
     assert all(a >= b for a, b in zip(apps, apps[1:]))
     assert apps[0] <= st["scratch_gate_apps"]
     assert apps[-1] < apps[0]
+
+
+@pytest.mark.parametrize("name,maker,shots", CIRCUITS, ids=[c[0] for c in CIRCUITS])
+def test_from_scratch_counts_match_plan(name, maker, shots):
+    # every leaf from |0..0>: N_l x G gate applications and the plan's Pauli
+    # count (the Kraus-branch choices select a gate's matrix, they are not
+    # Pauli applications)
+    pl = T.plan(maker(), shots, 3)
+    st = pl.stats()
+    cs = T.tusq_compile_stats(pl, T.run_opts(traversal=T.FROM_SCRATCH))
+    assert cs["gate_apps"] == st["scratch_gate_apps"]
+    assert cs["pauli_apps"] == st["scratch_pauli_apps"]

@@ -27,6 +27,26 @@ def test_option_range_checked_on_the_host():
         T.tusq_compile_stats(pl, T.run_opts(subtrees=17))
 
 
+@pytest.mark.parametrize("maker,shots", [
+    (lambda: W.brickwork(8, 10, 3, 5e-3, 3e-2), 20_000),
+    (lambda: W.repetition_memory(3, 2, 1, 2e-2, 3e-2, 2e-2), 4000),
+])
+@pytest.mark.parametrize("k", [2, 5])
+def test_chunk_programs_sum_to_the_oracle(maker, shots, k):
+    # the host side of the subtree cut: each chunk's device program
+    # (interpreted on the host) starts from |0..0>, and the chunks' outputs
+    # add up to the whole distribution
+    from tests.test_schedule_emulated import emu_run
+    c = maker()
+    ref, _ = oracle.run(c, shots, 3)
+    pl = T.plan(c, shots, 3)
+    total = np.zeros(1 << c.n_qubits)
+    for r in range(k):
+        got, _ = emu_run(pl.shard(r, k), precision=T.C128, traversal=T.DFTT, drift_tol=-1.0)
+        total += got
+    assert np.abs(total - ref).max() < 1e-12
+
+
 def _gpu(plan, **kw):
     import torch
     probs, info = T.run_torch(plan, T.run_opts(**kw))

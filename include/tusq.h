@@ -245,6 +245,9 @@ typedef struct {
                                  one state of device memory on top of snapshot_bytes. */
     int subtrees;             /* parallel-subtree DFTT on one GPU (Sec. III-B, subtrees traversed
                                  in parallel when memory is free): 1 (default) = one traversal;
+                                 -1 = automatic (enough chunks that the passes in flight offer
+                                 about twice the GPU's CTA slots: 16 for tiny states, 1 once a
+                                 single pass has that many tiles);
                                  k in 2..16 = the DFS order cut into k chunks of nearly equal work
                                  (as tusq_plan_shard), each traversed by its own exec on its own
                                  stream from its own copy of the root state, the k FP64 outputs

@@ -189,6 +189,25 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
                                    sizeof(uint64_t) * (pg.term_mask.size() + pg.term_phi.size()));
 }
 
+// Qubits of a full pass window (the tile of one CTA).
+static int tile_bits(int n, const tusq_run_opts *o) {
+    int L = o->precision == TUSQ_C128 ? 12 : 13;
+    if (o->max_window > 0) L = std::min(L, o->max_window);
+    return std::min(L, n);
+}
+
+// subtrees = -1: enough chunks that the passes in flight offer about twice
+// the CTA slots of the GPU (slots = SMs x CTAs per SM), at most 16; one
+// chunk when a single pass already has that many tiles.
+static int auto_subtrees(int n, const tusq_run_opts *o, uint64_t slots) {
+    const uint64_t tiles = 1ull << (n - tile_bits(n, o));
+    const uint64_t k = (2 * slots + tiles - 1) / tiles;
+    return (int)std::min<uint64_t>(std::max<uint64_t>(k, 1), 16);
+}
+
+// Parallel subtrees: the plan's DFS order cut into k chunks (tusq_plan_shard),
+// one exec per chunk on its own non-blocking stream, an FP64 output per
+// chunk after the first.
 // Device bytes an exec of this plan needs (state + snapshots + program).
 size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
     size_t amp = o->precision == TUSQ_C128 ? 16 : 8;
@@ -199,7 +218,9 @@ size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
         K = co.cache_states < 0 ? (int)std::min<uint64_t>(p->stats.n_noninv_layers, kDefaultCacheStates)
                                 : co.cache_states;
     const size_t one = state * (1 + co.snapshots + K) + (1u << 20);
-    const uint64_t parts = o->subtrees > 1 ? std::min<uint64_t>((uint64_t)o->subtrees, std::max<uint64_t>(p->n_inst(), 1)) : 1;
+    // (auto: the same rule with 148 SMs and the launch bounds' CTAs per SM)
+    const int k = o->subtrees < 0 ? auto_subtrees(p->n, o, o->precision == TUSQ_C128 ? 148 : 296) : o->subtrees;
+    const uint64_t parts = k > 1 ? std::min<uint64_t>((uint64_t)k, std::max<uint64_t>(p->n_inst(), 1)) : 1;
     return one * parts + (parts - 1) * sizeof(double) * ((size_t)1 << p->n);
 }
 
@@ -220,11 +241,8 @@ int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t 
 int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out);
 void exec_free(tusq_exec *e);
 
-// Parallel subtrees: the plan's DFS order cut into k chunks (tusq_plan_shard),
-// one exec per chunk on its own non-blocking stream, an FP64 output per
-// chunk after the first.
-static int create_parts(tusq_exec *e, const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t) {
-    const int k = (int)std::min<uint64_t>((uint64_t)o->subtrees, p->n_inst());
+static int create_parts(tusq_exec *e, const tusq_plan_t *p, const tusq_run_opts *o, int k_req) {
+    const int k = (int)std::min<uint64_t>((uint64_t)k_req, p->n_inst());
     tusq_run_opts so = *o;
     so.subtrees = 1;
     so.use_graph = 0;
@@ -265,8 +283,14 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e->nsm <= 0) e->nsm = 148;
-    if (o->subtrees > 1 && p->n_inst() >= 2) {
-        const int rc = create_parts(e, p, o, st);
+    int k_parts = o->subtrees;
+    if (k_parts < 0) {
+        const int L = tile_bits(p->n, o);
+        const int V = std::min(o->precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, L);
+        k_parts = auto_subtrees(p->n, o, (uint64_t)e->nsm * pass_occupancy(o->precision, V, L));
+    }
+    if (k_parts > 1 && p->n_inst() >= 2) {
+        const int rc = create_parts(e, p, o, k_parts);
         if (rc != TUSQ_OK) {
             exec_free(e);
             return rc;
@@ -592,8 +616,8 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
         set_error(std::string(who) + ": bad precision");
         return TUSQ_EINVAL;
     }
-    if (o.subtrees < 0 || o.subtrees > 16) {
-        set_error(std::string(who) + ": subtrees must be in [0, 16]");
+    if (o.subtrees < -1 || o.subtrees > 16) {
+        set_error(std::string(who) + ": subtrees must be in [-1, 16]");
         return TUSQ_EINVAL;
     }
     if (o.cache_states < -1 || o.cache_states > 64) {

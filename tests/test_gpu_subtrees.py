@@ -23,8 +23,10 @@ def close(got, ref, precision, what=""):
 def test_option_range_checked_on_the_host():
     pl = T.plan(W.random_layers(4, 3, 1, 1e-2, 1e-2), 1000, 0)
     T.tusq_compile_stats(pl, T.run_opts(subtrees=16))
-    with pytest.raises(T.TusqError):
-        T.tusq_compile_stats(pl, T.run_opts(subtrees=17))
+    T.tusq_compile_stats(pl, T.run_opts(subtrees=-1))
+    for bad in (17, -2):
+        with pytest.raises(T.TusqError):
+            T.tusq_compile_stats(pl, T.run_opts(subtrees=bad))
 
 
 @pytest.mark.parametrize("maker,shots", [
@@ -123,3 +125,14 @@ def test_six_qubit_configuration_with_many_chunks(k):
         info = ex.finish()
         assert info["unrecovered"] == 0
         close(out.cpu().numpy(), ref, T.C128, f"k {k}")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [6, 12, 18])
+def test_automatic_chunk_count(n):
+    c = W.brickwork(n, 8, n, 2e-3, 2e-2)
+    ref, _ = oracle.run(c, 20_000, 4)
+    pl = T.plan(c, 20_000, 4)
+    for precision in (T.C128, T.C64):
+        got, info = _gpu(pl, precision=precision, traversal=T.DFTT_SNAPSHOT, subtrees=-1)
+        close(got, ref, precision, f"n {n}")

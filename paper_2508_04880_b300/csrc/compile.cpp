@@ -845,7 +845,8 @@ struct Compiler {
             // without the branch stack, still end a pass at the next branch
             // node, so that the leaf pass that skips its write holds no op
             // above the node the uncompute returns to
-            if (!track && !scratch && i + 1 < N && P.lcp[i] > t_in && P.lcp[i] <= G) splits.push_back(P.lcp[i]);
+            if (!track && !scratch && co.leaf_peek && i + 1 < N && P.lcp[i] > t_in && P.lcp[i] <= G)
+                splits.push_back(P.lcp[i]);
             if (K > 0)
                 for (int j = t_in + 1; j < G; ++j)
                     if (layer_start[j]) splits.push_back(j);

@@ -1,25 +1,29 @@
 """GPU parity at full size, in the launch configuration the benchmark times
-(complex64 state, default 13-qubit pass window, snapshot traversal).
+(complex64 state, default 13-qubit pass window).
 
-The 28-qubit QAOA workload (random 3-regular graph, 4 layers, 2q
-depolarizing 5e-3, 1q 5e-4, 1e6 shots, alpha 0.01, beta 100) is too large
-for the oracle to follow over all 101 kept instances, so it is checked in
-two ways:
+28-qubit QAOA (random 3-regular graph, 4 layers, 2q depolarizing 5e-3, 1q
+5e-4, 1e6 shots, alpha 0.01, beta 100 -> 101 kept instances).  The oracle
+costs about a minute per instance at this size, so the comparison over all
+2^28 outcomes runs on an instance subset planned by the oracle: the first
+eight leaves in DFS order plus the ideal instance (the last leaf), with
+their weights.  As one plan of nine leaves it has branch nodes at several
+depths, so it exercises branch snapshots, restores fused into the next
+pass's tile loads, the leaf pass that skips its write, and -- in the
+uncompute traversal -- the drift check at every return (Sec. III-B).  Both
+the snapshot traversal and the paper's uncompute traversal are compared
+element by element (max-abs 1e-5, total variation 1e-4).  The whole
+101-leaf traversal is checked against properties that hold at any size.
 
-* an instance subset -- the first leaf in DFS order and the ideal instance
-  (the last leaf) with their weights, planned by the oracle -- runs through
-  the engine as a plan of its own and through the oracle from |0..0>, and
-  the two distributions are compared element by element over all 2^28
-  outcomes (max-abs 1e-5, total variation 1e-4);
-* the whole traversal is checked against properties that hold at any size:
-  the distribution sums to the sum of the weights, and the uncompute,
-  from-scratch and snapshot traversals agree.
+20-qubit brickwork, depth 40 (Haar SU(2) on every qubit and CZ on
+alternating neighbour pairs, 1180 gates), 1q/2q depolarizing 1e-3/1e-2, 1e6
+shots, pruned: the whole 101-leaf plan against the oracle, in complex64
+(1e-5 / 1e-4) and in the complex128 mode (1e-12 / 1e-10).
 
-The largest state the benchmark's serving mix admits (30 qubits, 8 GiB) is
-checked against a closed form: a GHZ circuit under Pauli noise, whose every
-instance is the ideal GHZ distribution XOR-shifted by the X part of its
-Pauli frame propagated to the end (Sec. II mixture view; Clifford
-conjugation of Paulis).
+The largest state the serving mix admits (30 qubits, 8 GiB) is checked
+against a closed form: a GHZ circuit under Pauli noise, whose every instance
+is the ideal GHZ distribution XOR-shifted by the X part of its Pauli frame
+propagated to the end (Sec. II mixture view; Clifford conjugation of
+Paulis).
 """
 import numpy as np
 import pytest
@@ -31,6 +35,7 @@ import tusq_workloads as W
 pytestmark = pytest.mark.gpu
 
 MAX_ABS, TV = 1e-5, 1e-4
+MAX_ABS_C128, TV_C128 = 1e-12, 1e-10
 
 
 def _torch():
@@ -45,21 +50,54 @@ def _run(plan, **opts):
     return probs, info
 
 
-def test_qaoa28_instance_subset_matches_oracle_elementwise():
+def _events(inst):
+    return [[tuple(int(v) for v in e) for e in ev] for ev in inst]
+
+
+def _compare(probs, ref, max_abs, tv, what):
+    torch = _torch()
+    d = (probs - torch.from_numpy(ref).to(probs.device)).abs()
+    m, s = float(d.max()), float(d.sum())
+    assert m <= max_abs, f"{what}: max-abs {m:.3e} > {max_abs}"
+    assert s <= tv, f"{what}: TV {s:.3e} > {tv}"
+    return m, s
+
+
+@pytest.fixture(scope="module")
+def qaoa28_subset():
     circ = W.WORKLOADS["qaoa_28q"]()
     opl = oracle.plan(circ, 1_000_000, 0)
     assert len(opl.inst) == 101 and len(opl.inst[-1]) == 0
-    subset = [list(opl.inst[0]), list(opl.inst[-1])]
-    weights = np.array([opl.weights[0], opl.weights[-1]])
+    idx = list(range(8)) + [len(opl.inst) - 1]
+    subset = [list(opl.inst[i]) for i in idx]
+    weights = np.array([opl.weights[i] for i in idx])
     ref = oracle.run_instances(circ, subset, weights)
-    pl = T.tusq_plan_from_instances(T.circuit_from(circ), [[tuple(int(v) for v in e) for e in ev] for ev in subset],
-                                    weights)
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), _events(subset), weights)
+    return circ, pl, ref, float(weights.sum())
+
+
+def test_qaoa28_nine_leaves_snapshot_traversal_matches_oracle(qaoa28_subset):
+    circ, pl, ref, wsum = qaoa28_subset
     probs, info = _run(pl, precision=T.C64, traversal=T.DFTT_SNAPSHOT)
-    got = probs.cpu().numpy()
-    d = np.abs(got - ref)
-    assert d.max() <= MAX_ABS, d.max()
-    assert d.sum() <= TV, d.sum()
-    assert info["leaf_passes"] == 2 and info["unrecovered"] == 0
+    _compare(probs, ref, MAX_ABS, TV, "28q nine leaves, snapshot traversal")
+    assert info["leaf_passes"] == 9 and info["unrecovered"] == 0
+    # every return to a branch node below the root is a snapshot restore
+    assert info["restores"] > 0
+    del probs
+    _torch().cuda.empty_cache()
+
+
+def test_qaoa28_nine_leaves_uncompute_traversal_matches_oracle(qaoa28_subset):
+    circ, pl, ref, wsum = qaoa28_subset
+    probs, info = _run(pl, precision=T.C64, traversal=T.DFTT, drift_tol=1e-6)
+    _compare(probs, ref, MAX_ABS, TV, "28q nine leaves, uncompute traversal")
+    # a drift check after every uncompute back to a branch node; complex64
+    # uncompute at 28 qubits drifts above 1e-6 at some nodes, which restore
+    # their snapshot, so none is left unrecovered
+    assert info["leaf_passes"] == 9 and info["checks"] > 0
+    assert info["unrecovered"] == 0
+    del probs
+    _torch().cuda.empty_cache()
 
 
 def test_qaoa28_full_traversal_properties():
@@ -81,6 +119,43 @@ def test_qaoa28_full_traversal_properties():
         assert float(d.sum()) <= TV, (name, float(d.sum()))
     del outs
     torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def brickwork20():
+    circ = W.WORKLOADS["brickwork_20q"]()
+    assert circ.n_qubits == 20 and circ.n_gates == 1180
+    opl = oracle.plan(circ, 1_000_000, 0)
+    ref = oracle.run_instances(circ, opl.inst, opl.weights)
+    return circ, opl, ref
+
+
+def test_brickwork20_depth40_plan_is_the_oracles(brickwork20):
+    circ, opl, ref = brickwork20
+    pl = T.plan(circ, 1_000_000, 0)
+    inst, counts, weights, lcp = pl.instances()
+    assert len(inst) == len(opl.inst) == 101
+    assert [tuple(ev) for ev in inst] == [tuple(tuple(int(v) for v in e) for e in ev) for ev in opl.inst]
+    assert np.array_equal(counts, opl.inst_count)
+    assert np.array_equal(weights, opl.weights)
+    assert np.array_equal(lcp, opl.lcp)
+
+
+@pytest.mark.parametrize("trav", [T.DFTT_SNAPSHOT, T.DFTT])
+def test_brickwork20_depth40_all_leaves_c64(brickwork20, trav):
+    circ, opl, ref = brickwork20
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), _events(opl.inst), opl.weights)
+    probs, info = _run(pl, precision=T.C64, traversal=trav)
+    _compare(probs, ref, MAX_ABS, TV, f"20q brickwork depth 40, complex64, traversal {trav}")
+    assert info["leaf_passes"] == 101 and info["unrecovered"] == 0
+
+
+def test_brickwork20_depth40_all_leaves_c128(brickwork20):
+    circ, opl, ref = brickwork20
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), _events(opl.inst), opl.weights)
+    probs, info = _run(pl, precision=T.C128, traversal=T.DFTT_SNAPSHOT)
+    _compare(probs, ref, MAX_ABS_C128, TV_C128, "20q brickwork depth 40, complex128")
+    assert info["leaf_passes"] == 101 and info["unrecovered"] == 0
 
 
 def _frame_xmask(circ, events):
@@ -115,8 +190,7 @@ def test_ghz30_closed_form_at_maximum_state_size():
         m = _frame_xmask(circ, [tuple(int(v) for v in e) for e in ev])
         idx += [m, m ^ ((1 << n) - 1)]
         val += [0.5 * w, 0.5 * w]
-    pl = T.tusq_plan_from_instances(T.circuit_from(circ), [[tuple(int(v) for v in e) for e in ev] for ev in opl.inst],
-                                    np.asarray(opl.weights))
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), _events(opl.inst), np.asarray(opl.weights))
     probs, info = _run(pl, precision=T.C64, traversal=T.DFTT, snapshot_bytes=2 * (8 << n))
     want = torch.zeros_like(probs)
     want.index_put_((torch.tensor(idx, device=probs.device),),

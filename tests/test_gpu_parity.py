@@ -150,9 +150,12 @@ def test_c64_vs_c128_brickwork():
     a, _ = gpu_run(pl, precision=T.C64, traversal=T.DFTT_SNAPSHOT)
     b, _ = gpu_run(pl, precision=T.C128, traversal=T.DFTT_SNAPSHOT)
     assert_close(a, b, T.C64)
-    inst, counts, w, lcp = pl.instances()
-    ref = oracle.run_instances(circ, inst, w, 0, 4)
-    sub = T.tusq_plan_from_instances(T.circuit_from(circ), inst[:4], w[:4])
+    # the oracle plans its own instances (no oracle input from the library)
+    opl = oracle.plan(circ, 100_000, 0)
+    inst = [[tuple(int(v) for v in e) for e in ev] for ev in opl.inst[:4]]
+    w = np.asarray(opl.weights[:4])
+    ref = oracle.run_instances(circ, inst, w)
+    sub = T.tusq_plan_from_instances(T.circuit_from(circ), inst, w)
     got, _ = gpu_run(sub, precision=T.C128)
     assert_close(got, ref, T.C128)
 

@@ -17,8 +17,12 @@ Also reported: gate-amplitude updates/s (executed, and the from-scratch
 equivalent N_l * G * 2^n), the HBM roofline of the fused pass kernel
 measured live with CUDA events around each pass launch, the end-to-end
 rate through the C ABI from host buffers (plan + compile + upload +
-traversal + copy of the distribution back), the oracle on the host cores
-as the CPU baseline, and SM clocks sampled during the timed region.
+traversal + copy of the distribution back), the paper's uncompute DFTT and
+the plain from-scratch GPU form timed beside the headline traversal, the
+error of each against the oracle on an instance subset the oracle plans
+itself, p50/p99 job latency of a short served run, the oracle on all host
+cores and on one core as the CPU baseline, and SM clocks sampled during the
+timed region.
 
 ``--impl reference`` times the CPU oracle (the reference arm): each step
 simulates a bounded prefix of the first instance of the same workload.
@@ -142,48 +146,96 @@ class ClockSampler:
 
 def traffic_from_profile(kernel_src: str):
     """Per-launch DRAM traffic of the pass kernel from the committed ncu
-    summary, scaled to bytes per algorithmic byte; None when the kernel
-    source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "pass_kernel_ncu.md")
+    summary (profiles/pass_kernel_ncu.json), as DRAM bytes per algorithmic
+    byte; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_ncu.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
     digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    fields = {}
-    for line in text.splitlines():
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
-            fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernels_cu_sha256_16") != digest:
+    if rec.get("kernels_cu_sha256_16") != digest:
         return None
     try:
-        return float(fields["dram_bytes_per_algorithmic_byte"])
-    except (KeyError, ValueError):
+        return float(rec["dram_bytes_per_algorithmic_byte"])
+    except (KeyError, TypeError, ValueError):
         return None
 
 
-def cpu_baseline(circ, plan_inst, budget_s: float = 15.0):
+def _omp_threads(k: int) -> None:
+    """Set the OpenMP team size of later parallel regions in this process
+    (the oracle's OpenMP runtime is the process's libgomp)."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(k))
+    except OSError:
+        pass
+
+
+def cpu_baseline(circ, plan_inst, budget_s: float = 15.0, threads: int = 0):
     """The oracle as it stands, timed on a bounded sample: a prefix of the
     first kept instance's gates (with its Pauli events), sized to about
-    budget_s of host work; the rate is scaled to instances/s."""
+    budget_s of host work; the rate is scaled to instances/s.  threads = 0:
+    every host core; otherwise the OpenMP team is limited to that many."""
     import oracle
+    oracle.lib()
+    all_cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = threads if threads > 0 else all_cores
+    _omp_threads(cores)
     G = circ.n_gates
     ev = list(plan_inst[0])
     k = 2
-    while True:
-        sub = W.Circuit(circ.n_qubits, circ.gates[:k], circ.channels[:k])
-        t0 = time.perf_counter()
-        oracle.simulate(sub, [e for e in ev if e[0] < k])
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 3 or k >= G:
-            break
-        k = min(G, max(k + 1, int(k * min(8.0, budget_s / max(dt, 1e-3)))))
+    try:
+        while True:
+            sub = W.Circuit(circ.n_qubits, circ.gates[:k], circ.channels[:k])
+            t0 = time.perf_counter()
+            oracle.simulate(sub, [e for e in ev if e[0] < k])
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 3 or k >= G:
+                break
+            k = min(G, max(k + 1, int(k * min(8.0, budget_s / max(dt, 1e-3)))))
+    finally:
+        _omp_threads(all_cores)
     rate = (k / G) / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": rate, "unit": "instances/s", "cores": cores, "kind": "oracle",
             "sample": f"first {k} of {G} gates of one instance ({circ.n_qubits} qubits, complex128), "
                       f"{dt:.2f} s, scaled by {G}/{k}"}
+
+
+def error_vs_oracle(T, torch, circ, shots, seed, arms, sp):
+    """Error of the engine against the oracle (complex128, every instance
+    simulated from |0..0> with no tree) on an instance subset of the
+    workload that the oracle plans itself: the first leaf in DFS order and
+    the ideal instance (the last leaf), with their weights.  The subset
+    runs through the engine as one plan under each arm's options; max-abs
+    and total variation over all 2^n outcomes."""
+    import oracle
+    t0 = time.perf_counter()
+    opl = oracle.plan(circ, shots, seed)
+    idx = [0, len(opl.inst) - 1]
+    subset = [[tuple(int(v) for v in e) for e in opl.inst[i]] for i in idx]
+    w = np.array([opl.weights[i] for i in idx])
+    ref = oracle.run_instances(circ, subset, w)
+    oracle_s = time.perf_counter() - t0
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), subset, w)
+    refd = torch.from_numpy(ref).to("cuda")
+    del ref
+    probs = torch.empty_like(refd)
+    per = {}
+    for name, o in arms:
+        ex = T.Exec(pl, o, sp)
+        ex.launch(probs.data_ptr(), sp)
+        ex.finish()
+        d = (probs - refd).abs()
+        per[name] = {"max_abs": float(d.max()), "tv": float(d.sum())}
+        del ex, d
+    del probs, refd
+    torch.cuda.empty_cache()
+    return {"instances_compared": len(idx), "subset": "first DFS leaf + ideal leaf, planned by the oracle",
+            "subset_weight": float(w.sum()), "tolerance": {"max_abs": 1e-5, "tv": 1e-4},
+            "max_abs": max(v["max_abs"] for v in per.values()), "tv": max(v["tv"] for v in per.values()),
+            "per_arm": per, "oracle_seconds": oracle_s}
 
 
 def run_reference(args, rank, world):
@@ -409,6 +461,45 @@ def run_caching(args, T, torch):
             "snapshot_ms": snap_ms, "snapshot_gate_apps": snap_info["gate_apps"], "uncompute": rows}
 
 
+def served_measure(T, torch, plans, n_inst, qubits, rates, slots, budget, seed=1):
+    """Serve `plans` through the serving loop: first all at once (capacity),
+    then with Poisson arrivals at each fraction of that capacity.  Returns
+    (capacity in jobs/s, per-rate latency and throughput rows)."""
+    outs = [torch.empty(1 << n, dtype=torch.float64, device="cuda") for n in qubits]
+    opts = T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT)
+    srv = T.Server(budget, n_streams=slots)
+    t0 = time.perf_counter()
+    for p, o in zip(plans, outs):
+        srv.submit(p, o.data_ptr(), opts)
+    srv.drain()
+    capacity = len(plans) / (time.perf_counter() - t0)
+    del srv
+    rng = np.random.default_rng(seed)
+    results = []
+    for frac in rates:
+        lam = frac * capacity
+        gaps = rng.exponential(1.0 / lam, len(plans))
+        srv = T.Server(budget, n_streams=slots)
+        t0 = time.perf_counter()
+        ids = []
+        for p, o in zip(plans, outs):
+            target = t0 + (gaps[:len(ids) + 1].sum())
+            while time.perf_counter() < target:
+                time.sleep(0.0002)
+            ids.append(srv.submit(p, o.data_ptr(), opts))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        lat = np.array([srv.poll(i)[1] for i in ids])
+        results.append({"rate_frac_of_capacity": frac, "rate_jobs_per_s": lam,
+                        "p50_latency_s": float(np.percentile(lat, 50)),
+                        "p99_latency_s": float(np.percentile(lat, 99)),
+                        "instances_per_s": sum(n_inst) / wall, "jobs_per_s": len(plans) / wall})
+        del srv
+    del outs
+    torch.cuda.empty_cache()
+    return capacity, results
+
+
 def run_served(args, T, torch):
     """Config 5: Poisson arrivals of jobs (10-30 qubits, depth 20-100, p in
     [1e-4, 1e-2], 1e5-1e6 shots) into the serving loop (admission by HBM
@@ -421,38 +512,9 @@ def run_served(args, T, torch):
     plans = [all_plans[j] for j in kept]
     del all_plans
     n_inst = [p.stats()["n_instances"] for p in plans]
-    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _ in stream_jobs]
     budget = int(args.hbm_budget_gb * (1 << 30))
-    results = []
-    # capacity: everything submitted at once
-    srv = T.Server(budget, n_streams=args.slots)
-    t0 = time.perf_counter()
-    ids = [srv.submit(p, o.data_ptr(), T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT))
-           for p, o in zip(plans, outs)]
-    srv.drain()
-    cap_s = time.perf_counter() - t0
-    capacity = len(plans) / cap_s
-    del srv
-    rng = np.random.default_rng(1)
-    for frac in args.rates:
-        lam = frac * capacity
-        gaps = rng.exponential(1.0 / lam, len(plans))
-        srv = T.Server(budget, n_streams=args.slots)
-        t0 = time.perf_counter()
-        ids = []
-        for p, o, g in zip(plans, outs, gaps):
-            target = t0 + (gaps[:len(ids) + 1].sum())
-            while time.perf_counter() < target:
-                time.sleep(0.0002)
-            ids.append(srv.submit(p, o.data_ptr(), T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT)))
-        srv.drain()
-        wall = time.perf_counter() - t0
-        lat = np.array([srv.poll(i)[1] for i in ids])
-        results.append({"rate_frac_of_capacity": frac, "rate_jobs_per_s": lam,
-                        "p50_latency_s": float(np.percentile(lat, 50)),
-                        "p99_latency_s": float(np.percentile(lat, 99)),
-                        "instances_per_s": sum(n_inst) / wall, "jobs_per_s": len(plans) / wall})
-        del srv
+    capacity, results = served_measure(T, torch, plans, n_inst, [c.n_qubits for c, _ in stream_jobs],
+                                       args.rates, args.slots, budget)
     return {"metric": "served noisy jobs: p50/p99 latency and instances/s", "unit": "s / instances/s",
             "capacity_jobs_per_s": capacity, "jobs": len(plans), "hbm_budget_gb": args.hbm_budget_gb,
             "jobs_offered": args.jobs, "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
@@ -460,6 +522,27 @@ def run_served(args, T, torch):
             "plan_seconds": plan_s,
             "qubits": [c.n_qubits for c, _ in stream_jobs], "rates": results, "dtype": "c64",
             "data": "synthetic"}
+
+
+def served_subrun(args, T, torch):
+    """A short served run for the headline line: args.served_jobs jobs of the
+    served stream (10-args.served_max_qubits qubits), Poisson arrivals at
+    args.served_rate x the measured capacity; p50/p99 job latency."""
+    all_jobs = W.served_stream(args.served_jobs, seed=0, n_hi=args.served_max_qubits)
+    kept, all_plans, rejected, plan_s = plan_admitted(T, [c for c, _ in all_jobs], lambda j: all_jobs[j][1],
+                                                      args.max_job_work, args.max_job_instances)
+    plans = [all_plans[j] for j in kept]
+    qubits = [all_jobs[j][0].n_qubits for j in kept]
+    del all_plans
+    n_inst = [p.stats()["n_instances"] for p in plans]
+    capacity, results = served_measure(T, torch, plans, n_inst, qubits, [args.served_rate], args.slots,
+                                       int(args.hbm_budget_gb * (1 << 30)))
+    r = results[0]
+    return {"jobs": len(plans), "jobs_offered": args.served_jobs, "qubits": f"10-{args.served_max_qubits}",
+            "rejected_over_work_budget": len(rejected), "capacity_jobs_per_s": capacity,
+            "rate_frac_of_capacity": args.served_rate, "p50_latency_s": r["p50_latency_s"],
+            "p99_latency_s": r["p99_latency_s"], "instances_per_s": r["instances_per_s"],
+            "plan_seconds": plan_s}
 
 
 def main():
@@ -474,7 +557,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-gates", type=int, default=12)
-    ap.add_argument("--compare", action="store_true", help="also time the other traversals")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other traversals (from scratch, uncompute DFTT) beside the headline")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the error against the oracle on an instance subset of the workload")
+    ap.add_argument("--no-served", action="store_true", help="skip the short served sub-run")
+    ap.add_argument("--served-jobs", type=int, default=16)
+    ap.add_argument("--served-max-qubits", type=int, default=26)
+    ap.add_argument("--served-rate", type=float, default=0.75)
     ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity", "caching"],
                     help="main: the 28-qubit headline; batch: config 4; served: config 5; "
                          "fidelity: pruning delta and per-stage ablation")
@@ -659,24 +749,38 @@ def main():
                                      "dftt_gate_apps", "scratch_gate_apps")},
         "clocks": clk.summary(),
     }
-    if args.compare and rank == 0:
+    # the paper's uncompute DFTT (drift check after every uncompute) and the
+    # plain GPU form (every instance from |0..0>) beside the headline
+    # traversal, each timed over two traversals after one warm-up, with the
+    # same kernels
+    arms = [("snapshot", T.run_opts(precision=prec, traversal=T.DFTT_SNAPSHOT)),
+            ("dftt_uncompute", T.run_opts(precision=prec, traversal=T.DFTT, drift_tol=1e-6)),
+            ("from_scratch", T.run_opts(precision=prec, traversal=T.FROM_SCRATCH))]
+    if not args.no_compare and rank == 0:
         other = {}
-        for name, tv in (("dftt", T.DFTT), ("scratch", T.FROM_SCRATCH), ("snapshot", T.DFTT_SNAPSHOT)):
-            e3 = T.Exec(plan, T.run_opts(precision=prec, traversal=tv), sp)
+        for name, o in arms:
+            e3 = T.Exec(plan, o, sp)
             e3.launch(probs.data_ptr(), sp)
             e3.finish()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            e3.launch(probs.data_ptr(), sp)
+            for _ in range(2):
+                e3.launch(probs.data_ptr(), sp)
             b.record(stream)
             inf3 = e3.finish()
-            other[name] = {"ms": a.elapsed_time(b), "passes": inf3["passes"],
-                           "instances_per_s": n_inst / (a.elapsed_time(b) / 1e3)}
+            t3 = a.elapsed_time(b) / 2
+            other[name] = {"ms": t3, "passes": inf3["passes"], "gate_apps": inf3["gate_apps"],
+                           "checks": inf3["checks"], "instances_per_s": n_inst / (t3 / 1e3)}
             del e3
         line["traversals"] = other
+    if not args.no_error and rank == 0 and args.workload.startswith("qaoa"):
+        line["error_vs_oracle"] = error_vs_oracle(T, torch, circ, shots, seed, arms, sp)
+    if not args.no_served and rank == 0:
+        line["served"] = served_subrun(args, T, torch)
     if rank == 0 and not args.no_cpu_baseline:
         inst = plan.instances()[0]
         line["cpu_baseline"] = cpu_baseline(circ, inst)
+        line["cpu_baseline_1core"] = cpu_baseline(circ, inst, budget_s=8.0, threads=1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -319,13 +319,36 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
 
 inline uint32_t swz(uint32_t e, bool c128) { return tile_swizzle(e, c128); }
 
-// Structure of a matrix op: real entries, or [[c, -is], [-is, c]].
+// Structure of a matrix op: real entries, or [[c, -is], [-is, c]] (RX-type;
+// tangent form SUB_RXT when |c| >= |s|, else SUB_RXS).
 uint32_t mat1_sub(const cd *m) {
     bool real = true;
     for (int k = 0; k < 4; ++k) real = real && m[k].imag() == 0.0;
     if (real) return SUB_REAL;
-    if (m[0] == m[3] && m[0].imag() == 0.0 && m[1] == m[2] && m[1].real() == 0.0) return SUB_RXTYPE;
+    if (m[0] == m[3] && m[0].imag() == 0.0 && m[1] == m[2] && m[1].real() == 0.0) {
+        const double c = m[0].real(), sn = -m[1].imag();
+        return std::fabs(c) >= std::fabs(sn) ? SUB_RXT : SUB_RXS;
+    }
     return SUB_GENERAL;
+}
+
+// The four matrix entries the kernels read for a 2x2 of form `sub`: the
+// matrix itself, or for the tangent forms the parameter in entry 0 (t = s/c
+// or k = c/s) with the factor taken out (c, or -is) multiplied into *K.
+void encode_mat1(const cd *m, uint32_t sub, cd *out, cd &K) {
+    if (sub == SUB_RXT || sub == SUB_RXS) {
+        const double c = m[0].real(), sn = -m[1].imag();
+        out[1] = out[2] = out[3] = 0;
+        if (sub == SUB_RXT) {
+            out[0] = sn / c;
+            K *= c;
+        } else {
+            out[0] = c / sn;
+            K *= cd(0, -sn);
+        }
+        return;
+    }
+    for (int k = 0; k < 4; ++k) out[k] = m[k];
 }
 
 // A 4x4 that exchanges two basis states and fixes the others (CX in some
@@ -507,6 +530,7 @@ struct Encoder {
                 pd.grow[i] = g;
                 pd.srow[i] = (uint16_t)swz(e, c128);
             }
+            cd Kpass = 1.0;   // the scalar the tangent forms of this launch take out
             for (size_t s = p0; s < p1; ++s) {
                 StageDesc &sd = pd.st[s - p0];
                 uint64_t R = pieces[s].R;
@@ -563,7 +587,7 @@ struct Encoder {
                         for (auto &z : pm) z = 0;
                         for (size_t k = oi; k < run_end; ++k) {
                             const int b = regidx[local[pops[k].q0]];
-                            for (int q = 0; q < 4; ++q) pm[4 * b + q] = pops[k].m[q];
+                            encode_mat1(pops[k].m, d.sub, pm + 4 * b, Kpass);
                             if (k > oi && last && last_uids) {
                                 last_uids->push_back(pops[k].uid);
                                 last_uids->insert(last_uids->end(), pops[k].merged.begin(), pops[k].merged.end());
@@ -583,8 +607,10 @@ struct Encoder {
                         d.sub = mat1_sub(o.m);
                         d.code = CODE_MAT1 + 5 * d.sub + (uint32_t)d.a;
                         d.mat = (uint32_t)(prog.mats.size() / 32);
+                        cd em[4];
+                        encode_mat1(o.m, d.sub, em, Kpass);
                         for (int k = 0; k < 16; ++k) {
-                            cd z = k < 4 ? o.m[k] : cd(0, 0);
+                            cd z = k < 4 ? em[k] : cd(0, 0);
                             prog.mats.push_back(z.real());
                             prog.mats.push_back(z.imag());
                         }
@@ -644,6 +670,18 @@ struct Encoder {
                     prog.ops.push_back(d);
                 }
                 sd.op_count = (uint32_t)(prog.ops.size() - sd.op_begin);
+            }
+            if (Kpass != cd(1.0, 0.0)) {
+                // the scalar goes on the first stage that multiplies by a
+                // per-thread phase anyway (it has a diagonal op), else on the last
+                int ks = -1;
+                for (int st = 0; st < pd.n_stages && ks < 0; ++st)
+                    for (uint32_t k = 0; k < pd.st[st].op_count; ++k)
+                        if (prog.ops[pd.st[st].op_begin + k].type == OP_DIAG) { ks = st; break; }
+                if (ks < 0) ks = pd.n_stages - 1;
+                pd.st[ks].kre = Kpass.real();
+                pd.st[ks].kim = Kpass.imag();
+                pd.st[ks].kflag = 1;
             }
             pd.nops = (uint32_t)prog.ops.size() - pd.op0;
             pd.nmat = (uint32_t)(prog.mats.size() / 32) - pd.mat0;

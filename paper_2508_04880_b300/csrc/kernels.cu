@@ -68,13 +68,22 @@ __device__ __forceinline__ void apply1(C2 (&a)[1 << V], C2 m0, C2 m1, C2 m2, C2 
             x.y = fma(m0.x, x.y, t1);
             y.x = fma(m3.x, y.x, t2);
             y.y = fma(m3.x, y.y, t3);
-        } else if constexpr (SUB == SUB_RXTYPE) {
-            // [[c, -is], [-is, c]] with c = m0.x, -s = m1.y
-            const auto t0 = m1.y * y.y, t1 = m1.y * y.x, t2 = m1.y * x.y, t3 = m1.y * x.x;
-            x.x = fma(m0.x, x.x, -t0);
-            x.y = fma(m0.x, x.y, t1);
-            y.x = fma(m0.x, y.x, -t2);
-            y.y = fma(m0.x, y.y, t3);
+        } else if constexpr (SUB == SUB_RXT) {
+            // [[1, -it], [-it, 1]], t = m0.x (the factor c is in the stage scalar)
+            const auto t = m0.x;
+            const auto xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+            x.x = fma(t, yi, xr);
+            x.y = fma(-t, yr, xi);
+            y.x = fma(t, xi, yr);
+            y.y = fma(-t, xr, yi);
+        } else if constexpr (SUB == SUB_RXS) {
+            // [[ik, 1], [1, ik]], k = m0.x (the factor -is is in the stage scalar)
+            const auto k = m0.x;
+            const auto xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+            x.x = fma(-k, xi, yr);
+            x.y = fma(k, xr, yi);
+            y.x = fma(-k, yi, xr);
+            y.y = fma(k, yr, xi);
         } else {
             const C2 xo = x, yo = y;
             const C2 u = cmad(m0, xo, cmul(m1, yo));
@@ -148,8 +157,11 @@ __device__ __forceinline__ void apply_matrix_op(typename C2T<R>::type (&a)[1 << 
     case CODE_MAT1 + 5 * SUB_REAL + B:                                                           \
         if constexpr (V > B) apply1<V, B, SUB_REAL>(a, m[0], m[1], m[2], m[3]);                 \
         break;                                                                                   \
-    case CODE_MAT1 + 5 * SUB_RXTYPE + B:                                                         \
-        if constexpr (V > B) apply1<V, B, SUB_RXTYPE>(a, m[0], m[1], m[2], m[3]);               \
+    case CODE_MAT1 + 5 * SUB_RXT + B:                                                            \
+        if constexpr (V > B) apply1<V, B, SUB_RXT>(a, m[0], m[1], m[2], m[3]);                  \
+        break;                                                                                   \
+    case CODE_MAT1 + 5 * SUB_RXS + B:                                                            \
+        if constexpr (V > B) apply1<V, B, SUB_RXS>(a, m[0], m[1], m[2], m[3]);                  \
         break;
 #define TUSQ_M2(X, Y)                                                                            \
     case CODE_MAT2 + pair_code(X, Y):                                                            \
@@ -165,7 +177,8 @@ __device__ __forceinline__ void apply_matrix_op(typename C2T<R>::type (&a)[1 << 
     switch (op.code) {
     case CODE_PROD + SUB_GENERAL: apply_prod<V, SUB_GENERAL>(a, (uint32_t)op.a, m); break;
     case CODE_PROD + SUB_REAL: apply_prod<V, SUB_REAL>(a, (uint32_t)op.a, m); break;
-    case CODE_PROD + SUB_RXTYPE: apply_prod<V, SUB_RXTYPE>(a, (uint32_t)op.a, m); break;
+    case CODE_PROD + SUB_RXT: apply_prod<V, SUB_RXT>(a, (uint32_t)op.a, m); break;
+    case CODE_PROD + SUB_RXS: apply_prod<V, SUB_RXS>(a, (uint32_t)op.a, m); break;
         TUSQ_M1(0) TUSQ_M1(1) TUSQ_M1(2) TUSQ_M1(3) TUSQ_M1(4)
         TUSQ_M2(0, 1) TUSQ_M2(0, 2) TUSQ_M2(0, 3) TUSQ_M2(0, 4) TUSQ_M2(1, 2)
         TUSQ_M2(1, 3) TUSQ_M2(1, 4) TUSQ_M2(2, 3) TUSQ_M2(2, 4) TUSQ_M2(3, 4)
@@ -360,8 +373,21 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
                     apply_diag<R, V>(a, op, P, gfix, acc);
                 }
             }
-            if (have_gfix) {
-                const C2 u = Phase<R>::unit(acc);
+            if (have_gfix || sd.kflag) {
+                // the per-thread constant phase and/or the pass's scalar
+                C2 u;
+                if (have_gfix) {
+                    u = Phase<R>::unit(acc);
+                } else {
+                    u.x = 1;
+                    u.y = 0;
+                }
+                if (sd.kflag) {
+                    C2 k;
+                    k.x = (R)sd.kre;
+                    k.y = (R)sd.kim;
+                    u = cmul(u, k);
+                }
 #pragma unroll
                 for (int r = 0; r < NR; ++r) a[r] = cmul(a[r], u);
             }

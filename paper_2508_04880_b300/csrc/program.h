@@ -17,9 +17,14 @@ constexpr int kRegBitsC128 = 4;      // 2^4 (complex128)
 enum DevOpType : int32_t { OP_MAT1 = 1, OP_MAT2 = 2, OP_DIAG = 3 };
 
 // Structure of a matrix op (DevOp::sub), chosen on the host so the kernel
-// spends fewer FMAs: MAT1 general / real entries / [[c, -is], [-is, c]];
-// MAT2 general / a swap of two basis states (CX in some basis order).
-enum DevOpSub : uint32_t { SUB_GENERAL = 0, SUB_REAL = 1, SUB_RXTYPE = 2, SUB_SWAP = 3 };
+// spends fewer FMAs.  MAT1: general; real entries; and the RX-type form
+// [[c, -is], [-is, c]] with a scalar factored out (tangent forms, two FMAs
+// per output amplitude):
+//   SUB_RXT (|c| >= |s|): c [[1, -it], [-it, 1]], t = s / c in entry 0;
+//   SUB_RXS (|s| >  |c|): -is [[ik, 1], [1, ik]], k = c / s in entry 0;
+// the factor (c, or -is) goes into the pass's scalar (StageDesc::kre/kim).
+// MAT2: general, or a swap of two basis states (CX in some basis order).
+enum DevOpSub : uint32_t { SUB_GENERAL = 0, SUB_REAL = 1, SUB_RXT = 2, SUB_RXS = 3, SUB_SWAP = 4 };
 
 #if defined(__CUDACC__)
 #define TUSQ_HD __host__ __device__ __forceinline__
@@ -59,13 +64,13 @@ struct DevOp {
 static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
 
 // Kernel dispatch code of an op: MAT1 = CODE_MAT1 + 5 sub + a (sub is
-// SUB_GENERAL, SUB_REAL or SUB_RXTYPE), MAT2 = CODE_MAT2 / CODE_SWAP + the
+// SUB_GENERAL, SUB_REAL, SUB_RXT or SUB_RXS), MAT2 = CODE_MAT2 / CODE_SWAP + the
 // index of the register pair (a, b) in (0,1) (0,2) (0,3) (0,4) (1,2) (1,3)
 // (1,4) (2,3) (2,4) (3,4) order, DIAG = CODE_DIAG.  A product op
 // (CODE_PROD + sub) is a run of 2x2s of one form on distinct register bits:
 // `a` is the mask of those bits and bit b's matrix is entries 4b..4b+3 of
 // the two matrix slots starting at `mat`.
-enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 16, CODE_SWAP = 32, CODE_DIAG = 48, CODE_PROD = 64 };
+enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DIAG = 64, CODE_PROD = 80 };
 
 TUSQ_HD constexpr uint32_t pair_code(int lo, int hi) {
     return (uint32_t)(lo * (9 - lo) / 2 + (hi - lo - 1));
@@ -78,6 +83,13 @@ struct StageDesc {
     uint8_t cglob[16];     // global position of each thread bit (win[cpos[i]])
     uint64_t greg[8];      // global bit of each register bit (1 << win[rbits[i]])
     uint32_t op_begin, op_count;
+    // kflag != 0: multiply every amplitude by kre + i kim when the stage
+    // ends -- the product of the factors the tangent forms of the pass took
+    // out (a scalar commutes with every op, so the compiler puts it on one
+    // stage of the pass, preferably one that multiplies by a per-thread
+    // phase anyway)
+    double kre, kim;
+    uint32_t kflag, kpad;
 };
 
 // Per-pass program limits: a pass's ops, matrices and diagonal terms are

@@ -77,24 +77,34 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                     const DevOp &op = pg.ops[sd.op_begin + k];
                     const double *m = &pg.mats[32 * (size_t)op.mat];
                     auto M = [&](int q) { return cd(m[2 * q], m[2 * q + 1]); };
-                    if (op.type == OP_MAT1 && op.code >= CODE_PROD) {
-                        // product op: bit b's 2x2 at matrix entries 4b..4b+3
-                        for (int bit = 0; bit < v; ++bit) {
-                            if (!(op.a >> bit & 1)) continue;
-                            for (int r = 0; r < (1 << v); ++r) {
-                                if (r >> bit & 1) continue;
-                                cd x = a[r], y = a[r | 1 << bit];
-                                a[r] = M(4 * bit) * x + M(4 * bit + 1) * y;
-                                a[r | 1 << bit] = M(4 * bit + 2) * x + M(4 * bit + 3) * y;
+                    // a 2x2 of form `sub` on register bit `bit`, entries from slot
+                    // offset e0; the tangent forms carry one parameter in entry e0
+                    // (their factor is the stage scalar)
+                    auto two_by_two = [&](int bit, int e0) {
+                        for (int r = 0; r < (1 << v); ++r) {
+                            if (r >> bit & 1) continue;
+                            cd x = a[r], y = a[r | 1 << bit];
+                            const cd I(0, 1);
+                            if (op.sub == SUB_RXT) {
+                                const double t = M(e0).real();
+                                a[r] = x - I * t * y;
+                                a[r | 1 << bit] = y - I * t * x;
+                            } else if (op.sub == SUB_RXS) {
+                                const double k = M(e0).real();
+                                a[r] = y + I * k * x;
+                                a[r | 1 << bit] = x + I * k * y;
+                            } else {
+                                a[r] = M(e0) * x + M(e0 + 1) * y;
+                                a[r | 1 << bit] = M(e0 + 2) * x + M(e0 + 3) * y;
                             }
                         }
+                    };
+                    if (op.type == OP_MAT1 && op.code >= CODE_PROD) {
+                        // product op: bit b's 2x2 at matrix entries 4b..4b+3
+                        for (int bit = 0; bit < v; ++bit)
+                            if (op.a >> bit & 1) two_by_two(bit, 4 * bit);
                     } else if (op.type == OP_MAT1) {
-                        for (int r = 0; r < (1 << v); ++r) {
-                            if (r >> op.a & 1) continue;
-                            cd x = a[r], y = a[r | 1 << op.a];
-                            a[r] = M(0) * x + M(1) * y;
-                            a[r | 1 << op.a] = M(2) * x + M(3) * y;
-                        }
+                        two_by_two(op.a, 0);
                     } else if (op.type == OP_MAT2) {
                         for (int r = 0; r < (1 << v); ++r) {
                             if ((r >> op.a & 1) || (r >> op.b & 1)) continue;
@@ -147,6 +157,8 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                         }
                     }
                 }
+                if (sd.kflag)
+                    for (int r = 0; r < (1 << v); ++r) a[r] *= cd(sd.kre, sd.kim);
                 for (int r = 0; r < (1 << v); ++r) tile[es[r]] = a[r];
             }
         }

@@ -255,11 +255,28 @@ typedef struct {
                                  pass does not fill the GPU (small states); costs k times the
                                  state, snapshot and cache memory.  tusq_compile_stats reports
                                  the single traversal. */
+    int tc_mode;              /* enum tusq_tc_mode: complex64 register stages whose ops are all
+                                 independent of the thread (matrix ops on the stage's register
+                                 qubits, diagonal terms within them; e.g. a layer of single-qubit
+                                 gates plus the CZs among those qubits) run as one 32x32 complex
+                                 matrix on the tensor cores instead of op by op (Sec. II, Eq. 1:
+                                 a fused gate block applied to groups of 2^k amplitudes).
+                                 TUSQ_TC_NONE (default) = never. Only 13-qubit pass tiles. */
 } tusq_run_opts;
+
+/* Tensor-core precision of the dense stages (FP32 accumulation in TMEM):
+ *   TF32X3  amplitudes and matrix split into TF32 hi + lo parts, three products
+ *           (hi.hi + hi.lo + lo.hi): about 1e-6 relative error per stage;
+ *   BF16X3  the same split in BF16: about 1e-4 relative error per stage;
+ *   TF32    one TF32 product: about 1e-3 relative error per stage.
+ * Only TF32X3 is meant to meet the complex64 tolerance of the output
+ * (max-abs 1e-5, total variation 1e-4) on deep circuits; the other two are
+ * for error studies. */
+enum tusq_tc_mode { TUSQ_TC_NONE = 0, TUSQ_TC_TF32X3 = 1, TUSQ_TC_BF16X3 = 2, TUSQ_TC_TF32 = 3 };
 
 /* Defaults: C64, window 0, DFTT, leaf_peek 1, root_reset 1, drift_tol 1e-6,
  * snapshot_bytes 0 = 64 states when they fit in 16 GiB, else 8 states,
- * cache_states -1, subtrees 1. */
+ * cache_states -1, subtrees 1, tc_mode TUSQ_TC_NONE. */
 void tusq_run_opts_default(tusq_run_opts *o);
 
 typedef struct {
@@ -338,6 +355,17 @@ void tusq_exec_free(tusq_exec *e);
 /* tusq_exec_create + launch + finish + free. */
 int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
              void *cuda_stream);
+
+/* Diagnostic of the tensor-core dense stage on the current device: y_t = U x_t
+ * for t = 0..255 through the same device path as a dense stage of a pass
+ * (one CTA of 256 threads, each holding one vector in registers).
+ *   u_host : host, row-major 32x32 complex matrix as 2048 doubles (re, im);
+ *   x_dev  : device, 256 x 32 complex64 (row t = vector t), read;
+ *   y_dev  : device, 256 x 32 complex64, written.
+ * Synchronises the stream.  TUSQ_EINVAL for a bad mode, TUSQ_ETIMEOUT if
+ * the wait for the tensor cores ran out, TUSQ_ECUDA on CUDA errors. */
+int tusq_dense_check(int tc_mode, const double *u_host, const float *x_dev, float *y_dev,
+                     void *cuda_stream);
 
 /* ------------------------------------------------------- shot sampling */
 

@@ -26,6 +26,7 @@ TUSQ_OK, TUSQ_EINVAL, TUSQ_ENOMEM, TUSQ_ENOMEM_ADMIT, TUSQ_ECUDA, TUSQ_EDRIFT, \
 C64, C128 = 0, 1
 COMMUTE_OFF, COMMUTE_PAPER, COMMUTE_CLIFFORD = 0, 1, 2
 DFTT, FROM_SCRATCH, DFTT_SNAPSHOT = 0, 1, 2
+TC_NONE, TC_TF32X3, TC_BF16X3, TC_TF32 = 0, 1, 2, 3
 
 # Every symbol include/tusq.h declares.
 EXPORTS = [
@@ -36,7 +37,7 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
-    "tusq_run", "tusq_run_noalloc", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
+    "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
@@ -73,7 +74,7 @@ class RunOpts(ctypes.Structure):
                 ("leaf_peek", ctypes.c_int), ("root_reset", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int), ("cache_states", ctypes.c_int),
-                ("subtrees", ctypes.c_int)]
+                ("subtrees", ctypes.c_int), ("tc_mode", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):
@@ -124,6 +125,7 @@ def _load():
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
+        "tusq_dense_check": (i32, [i32, P(f64), vp, vp, vp]),
         "tusq_sample": (i32, [vp, i32, u64, u64, vp, vp]),
         "tusq_batch_create": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), i32, vp, P(vp)]),
         "tusq_batch_launch": (i32, [vp, vp]),
@@ -388,6 +390,15 @@ def tusq_run_noalloc(plan: Plan, probs_ptr: int, opts: Optional[RunOpts] = None,
     _check(lib.tusq_run_noalloc(plan.h, ctypes.byref(o), ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream),
                                 ctypes.byref(info)))
     return info.as_dict()
+
+
+def tusq_dense_check(tc_mode: int, u, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    """y_t = U x_t (t = 0..255, vectors of 32 complex64 amplitudes) through the
+    tensor-core dense-stage path; u is a 32x32 complex array."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(32, 32)).view(np.float64)
+    _check(lib.tusq_dense_check(tc_mode, uu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream)),
+           "tusq_dense_check")
 
 
 def tusq_sample(probs_ptr: int, n_qubits: int, shots: int, seed: int, counts_ptr: int, stream: int = 0) -> None:

@@ -628,6 +628,10 @@ static int resolve_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_ru
         set_error(std::string(who) + ": bad traversal");
         return TUSQ_EINVAL;
     }
+    if (o.tc_mode < TUSQ_TC_NONE || o.tc_mode > TUSQ_TC_TF32) {
+        set_error(std::string(who) + ": tc_mode must be TUSQ_TC_NONE, TUSQ_TC_TF32X3, TUSQ_TC_BF16X3 or TUSQ_TC_TF32");
+        return TUSQ_EINVAL;
+    }
     if (o.max_window != 0 && (o.max_window < 4 || o.max_window > kMaxTileBits)) {
         set_error(std::string(who) + ": max_window must be 0 (default) or in [4, 14]");
         return TUSQ_EINVAL;

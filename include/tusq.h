@@ -300,6 +300,7 @@ typedef struct {
     uint64_t cache_restores;      /* DFTT+Caching: returns served by a cached pre-layer state */
     uint64_t rederives;           /* returns re-derived forward from a snapshot above or |0..0>
                                      (no usable state below a non-invertible layer) */
+    uint64_t dense_ops;           /* tensor-core dense ops (tc_mode): 32x32 matrices */
 } tusq_run_info_t;
 
 /* Compile a plan into a device program for the current device and allocate
@@ -318,7 +319,8 @@ int tusq_exec_launch(tusq_exec *e, double *probs_dev, void *cuda_stream);
 
 /* Synchronise the stream of the last launch and fill *info; returns
  * TUSQ_EDRIFT if a check failed where no snapshot was available, or
- * TUSQ_ETIMEOUT if a device wait expired. */
+ * TUSQ_ETIMEOUT if a bounded device wait ran out (the only waits are those of
+ * the tensor-core dense stages, tc_mode != TUSQ_TC_NONE). */
 int tusq_exec_finish(tusq_exec *e, tusq_run_info_t *info);
 
 /* Host only (no GPU needed): compile the plan's device program with `opts`
@@ -340,7 +342,7 @@ int tusq_exec_pass_profile(tusq_exec *e, uint64_t *n_passes, const float **ms,
                            const double **bytes);
 
 /* Structure of every pass of the compiled program, in launch order, 8
- * integers per pass: register stages, ops, 2x2 ops, 4x4 ops, diagonal ops,
+ * integers per pass: register stages, ops, 2x2 ops, 4x4 and dense ops, diagonal ops,
  * diagonal terms, flags (1 write, 2 snapshot, 4 leaf, 8 reduce), tile
  * qubits.  Borrowed, valid until tusq_exec_free. */
 int tusq_exec_pass_structure(tusq_exec *e, uint64_t *n_passes, const int32_t **fields);
@@ -349,6 +351,15 @@ int tusq_exec_pass_structure(tusq_exec *e, uint64_t *n_passes, const int32_t **f
  * taken from now on (0 = off).  Forces the drift path without touching the
  * device state. */
 int tusq_exec_set_record_bias(tusq_exec *e, double delta);
+
+/* Test hook for the bounded waits of the tensor-core dense stages: when on,
+ * later launches (not already captured into a CUDA graph) skip issuing the
+ * tensor-core work of every dense op, so each CTA's wait for it runs out
+ * after about one second of SM clock; the kernel then records the timeout,
+ * stops its CTA's work, frees its tensor memory and returns, and
+ * tusq_exec_finish returns TUSQ_ETIMEOUT.  The output is then incomplete.
+ * Nothing faults or hangs; the context stays usable. */
+int tusq_exec_set_dense_skip(tusq_exec *e, int on);
 
 void tusq_exec_free(tusq_exec *e);
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "tusq_plan_n_qubits", "tusq_plan_shard", "tusq_plan_free", "tusq_run_opts_default",
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
-    "tusq_exec_set_profiling", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
+    "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
     "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_server_drain",
@@ -84,7 +84,7 @@ class RunInfo(ctypes.Structure):
         [(f, ctypes.c_double) for f in ("max_drift", "state_bytes", "algorithmic_bytes",
                                         "program_bytes")] + \
         [(f, ctypes.c_uint64) for f in ("stages", "matrix_ops", "diag_ops", "diag_terms", "cache_restores",
-                                        "rederives")]
+                                        "rederives", "dense_ops")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -120,6 +120,7 @@ def _load():
         "tusq_exec_set_record_bias": (i32, [vp, f64]),
         "tusq_compile_stats": (i32, [vp, P(RunOpts), P(RunInfo)]),
         "tusq_exec_set_profiling": (i32, [vp, i32]),
+        "tusq_exec_set_dense_skip": (i32, [vp, i32]),
         "tusq_exec_pass_profile": (i32, [vp, P(u64), P(P(ctypes.c_float)), P(P(f64))]),
         "tusq_exec_pass_structure": (i32, [vp, P(u64), P(P(ctypes.c_int32))]),
         "tusq_exec_free": (None, [vp]),
@@ -339,6 +340,9 @@ class Exec:
 
     def set_record_bias(self, delta: float) -> None:
         _check(lib.tusq_exec_set_record_bias(self.h, delta))
+
+    def set_dense_skip(self, on: bool) -> None:
+        _check(lib.tusq_exec_set_dense_skip(self.h, int(bool(on))))
 
     def set_profiling(self, on: bool) -> None:
         _check(lib.tusq_exec_set_profiling(self.h, int(bool(on))))

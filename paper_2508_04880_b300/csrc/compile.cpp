@@ -25,7 +25,7 @@ namespace {
 
 // ----------------------------------------------------------------- host ops
 
-enum HType { H_MAT1 = 0, H_MAT2 = 1, H_DIAG = 2 };
+enum HType { H_MAT1 = 0, H_MAT2 = 1, H_DIAG = 2, H_DENSE = 3 };
 
 struct HOp {
     int type = H_MAT1;
@@ -38,6 +38,11 @@ struct HOp {
     cd m[16];
     double phi0 = 0;              // DIAG, in turns
     std::vector<std::pair<uint64_t, double>> terms;   // (global mask, turns)
+    // H_DENSE: a run of thread-independent ops of one register stage as one
+    // 32x32 matrix in the register basis (row-major, <i|U|j>), applied on the
+    // tensor cores; phi0 / terms then hold the absorbed diagonal terms on
+    // fixed (non-register) bits only, a per-thread constant phase
+    std::vector<cd> du;
     uint64_t qmask() const {
         if (type == H_DIAG) {
             uint64_t m = 0;
@@ -376,6 +381,29 @@ bool mat2_swap(const cd *m, int &s0, int &s1) {
     return true;
 }
 
+// SIMT cost of an op in FP32 instructions per amplitude (register-stage
+// estimate used to decide which thread-independent runs go to the tensor
+// cores): a general 2x2 is 8, a real one 4, the tangent forms 2, a 4x4 16, a
+// basis swap 6, each register-mask group of a diagonal run 2.
+double simt_cost(const HOp &o, const uint64_t *greg, int v) {
+    if (o.type == H_MAT1) {
+        const uint32_t sub = mat1_sub(o.m);
+        return sub == SUB_GENERAL ? 8.0 : sub == SUB_REAL ? 4.0 : 2.0;
+    }
+    if (o.type == H_MAT2) {
+        int s0, s1;
+        return mat2_swap(o.m, s0, s1) ? 6.0 : 16.0;
+    }
+    uint32_t groups = 0;
+    for (auto &t : o.terms) {
+        int mu = 0;
+        for (int i = 0; i < v; ++i)
+            if (t.first & greg[i]) mu |= 1 << i;
+        groups |= 1u << mu;
+    }
+    return 2.0 * __builtin_popcount(groups & ~1u) + 0.5;
+}
+
 uint64_t to_fixed(double turns, bool c128) {
     double f = turns - std::floor(turns);
     if (c128) {
@@ -392,6 +420,134 @@ struct Encoder {
     int V;
     int Lmax;
     bool lookahead = true;
+    int tc_mode = TUSQ_TC_NONE;
+
+    // Program bytes of one op in shared memory.
+    uint32_t op_bytes(const HOp &o) const {
+        const uint32_t mb = c128 ? 256u : 128u;
+        if (o.type == H_DIAG) return (uint32_t)sizeof(DevOp) + 16 * (uint32_t)o.terms.size();
+        if (o.type == H_DENSE)
+            return (uint32_t)sizeof(DevOp) + 16 * (uint32_t)o.terms.size() +
+                   (uint32_t)(dense_b_words(tc_mode) / 32) * mb;
+        return (uint32_t)sizeof(DevOp) + mb;
+    }
+
+    // Tensor-core form of one register stage (Sec. II, Eq. 1: consecutive
+    // gates on the same 2^k amplitudes multiply into one matrix).  R is the
+    // stage's register mask over local bits, win the pass window.  Matrix ops
+    // act on register bits with one matrix for every thread; a diagonal op is
+    // thread-independent when none of its terms mixes register and fixed
+    // bits -- its register-only terms join the matrix, its fixed-only terms
+    // are a per-thread constant phase that commutes with the whole stage and
+    // rides along on the dense op.  A diagonal op with a mixed term stays a
+    // SIMT op and ends the run.  Runs whose SIMT cost reaches kDenseMinCost
+    // become one H_DENSE op.
+    std::vector<HOp> densify(const std::vector<HOp> &ops, uint64_t R, const std::vector<int> &win) const {
+        const int L = (int)win.size();
+        const int v = std::min(V, L);
+        int local[64];
+        for (int i = 0; i < 64; ++i) local[i] = -1;
+        for (int i = 0; i < L; ++i) local[win[i]] = i;
+        int regidx[64];
+        for (int i = 0; i < 64; ++i) regidx[i] = -1;
+        uint64_t greg[8] = {0};
+        uint64_t rg = 0;
+        {
+            int k = 0;
+            for (int b = 0; b < L; ++b)
+                if (R >> b & 1) {
+                    regidx[b] = k;
+                    greg[k] = 1ULL << win[b];
+                    rg |= greg[k];
+                    ++k;
+                }
+        }
+        std::vector<HOp> out, run;
+        auto flush = [&]() {
+            double cost = 0;
+            for (const HOp &o : run) cost += simt_cost(o, greg, v);
+            if (run.empty() || cost < kDenseMinCost) {
+                out.insert(out.end(), run.begin(), run.end());
+                run.clear();
+                return;
+            }
+            HOp d;
+            d.type = H_DENSE;
+            d.key = run.front().key;
+            d.uid = run.front().uid;
+            d.du.assign(32 * 32, cd(0, 0));
+            for (int i = 0; i < 32; ++i) d.du[33 * i] = 1.0;
+            std::vector<cd> nu(32 * 32);
+            for (const HOp &o : run) {
+                if (&o != &run.front()) {
+                    d.merged.push_back(o.uid);
+                }
+                d.merged.insert(d.merged.end(), o.merged.begin(), o.merged.end());
+                // M_o (32x32 in the register basis), then U <- M_o U
+                std::vector<cd> m(32 * 32, cd(0, 0));
+                if (o.type == H_MAT1) {
+                    const int b = regidx[local[o.q0]];
+                    for (int r = 0; r < 32; ++r) {
+                        if (r >> b & 1) continue;
+                        const int r1 = r | 1 << b;
+                        m[32 * r + r] = o.m[0];
+                        m[32 * r + r1] = o.m[1];
+                        m[32 * r1 + r] = o.m[2];
+                        m[32 * r1 + r1] = o.m[3];
+                    }
+                } else if (o.type == H_MAT2) {
+                    const int ra = regidx[local[o.q0]], rb = regidx[local[o.q1]];
+                    for (int r = 0; r < 32; ++r)
+                        for (int c = 0; c < 32; ++c) {
+                            const int outside = ~((1 << ra) | (1 << rb)) & 31;
+                            if ((r & outside) != (c & outside)) continue;
+                            const int lr = 2 * (r >> ra & 1) + (r >> rb & 1);
+                            const int lc = 2 * (c >> ra & 1) + (c >> rb & 1);
+                            m[32 * r + c] = o.m[4 * lr + lc];
+                        }
+                } else {
+                    // register-only terms into the matrix; fixed-only ones ride along
+                    d.phi0 += o.phi0;
+                    for (int r = 0; r < 32; ++r) {
+                        double turns = 0;
+                        for (auto &t : o.terms) {
+                            if ((t.first & rg) == 0) continue;
+                            int mu = 0;
+                            for (int i = 0; i < v; ++i)
+                                if (t.first & greg[i]) mu |= 1 << i;
+                            if (__builtin_popcount(r & mu) & 1) turns += t.second;
+                        }
+                        m[32 * r + r] = std::polar(1.0, 2 * kPi * turns);
+                    }
+                    for (auto &t : o.terms)
+                        if ((t.first & rg) == 0) d.terms.push_back(t);
+                }
+                for (int r = 0; r < 32; ++r)
+                    for (int c = 0; c < 32; ++c) {
+                        cd acc = 0;
+                        for (int k = 0; k < 32; ++k) acc += m[32 * r + k] * d.du[32 * k + c];
+                        nu[32 * r + c] = acc;
+                    }
+                d.du.swap(nu);
+            }
+            out.push_back(d);
+            run.clear();
+        };
+        for (const HOp &o : ops) {
+            bool indep = true;
+            if (o.type == H_DIAG)
+                for (auto &t : o.terms)
+                    if ((t.first & rg) && (t.first & ~rg)) { indep = false; break; }
+            if (indep) {
+                run.push_back(o);
+            } else {
+                flush();
+                out.push_back(o);
+            }
+        }
+        flush();
+        return out;
+    }
 
     // Encode one pass (window + ops already in application order) into
     // PassDescs: several when the register stages exceed kMaxStages or the
@@ -458,42 +614,57 @@ struct Encoder {
                 (void)taken;
             }
             std::vector<HOp> merged = merge_ops(ordered);
+            // the register bits the stage will use (filled up to v with the
+            // highest unused local bits, as the encoding below does)
+            uint64_t Rs = swin[s];
+            for (int b = L - 1; b >= 0 && __builtin_popcountll(Rs) < v; --b) Rs |= 1ULL << b;
+            if (tc_mode != TUSQ_TC_NONE && !c128 && L == kDenseTileBits && v == kRegBitsC64)
+                merged = densify(merged, Rs, win);
             // cut into pieces of at most kMaxStageOps ops and at most the
             // per-pass program budget (same register bits)
-            Piece cur{swin[s], {}};
+            Piece cur{Rs, {}};
             uint32_t cur_bytes = 0;
+            bool cur_dense = false;
             for (const HOp &o : merged) {
-                uint32_t ob = (uint32_t)sizeof(DevOp) +
-                              (o.type == H_DIAG ? 16 * (uint32_t)o.terms.size() : (c128 ? 256u : 128u));
-                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > kMaxPassProgramBytes)) {
+                const uint32_t ob = op_bytes(o);
+                const bool dn = cur_dense || o.type == H_DENSE;
+                const uint32_t cap = dn ? kMaxDensePassProgramBytes : kMaxPassProgramBytes;
+                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > cap)) {
                     pieces.push_back(cur);
                     cur.ops.clear();
                     cur_bytes = 0;
+                    cur_dense = false;
                 }
                 cur.ops.push_back(o);
                 cur_bytes += ob;
+                cur_dense = cur_dense || o.type == H_DENSE;
             }
             if (!cur.ops.empty()) pieces.push_back(cur);
         }
         const uint32_t mat_bytes = c128 ? 256 : 128;
         auto piece_bytes = [&](const Piece &pc) {
             uint32_t b = 0;
-            for (const HOp &o : pc.ops) {
-                b += sizeof(DevOp);
-                if (o.type == H_DIAG) b += 16 * (uint32_t)o.terms.size();
-                else b += mat_bytes;
-            }
+            for (const HOp &o : pc.ops) b += op_bytes(o);
             return b;
+        };
+        auto piece_dense = [&](const Piece &pc) {
+            for (const HOp &o : pc.ops)
+                if (o.type == H_DENSE) return true;
+            return false;
         };
         size_t p0 = 0;
         do {
-            // as many pieces as the stage and program limits allow
+            // as many pieces as the stage and program limits allow (the larger
+            // budget once a piece with dense ops is in)
             size_t p1 = p0;
             uint32_t bytes = 0;
+            bool dense = false;
             while (p1 < pieces.size() && (int)(p1 - p0) < kMaxStages) {
                 uint32_t b = piece_bytes(pieces[p1]);
-                if (p1 > p0 && bytes + b > kMaxPassProgramBytes) break;
+                const bool dn = dense || piece_dense(pieces[p1]);
+                if (p1 > p0 && bytes + b > (dn ? kMaxDensePassProgramBytes : kMaxPassProgramBytes)) break;
                 bytes += b;
+                dense = dn;
                 ++p1;
             }
             PassDesc pd;
@@ -640,6 +811,41 @@ struct Encoder {
                         d.sw0 = (int16_t)s0;
                         d.sw1 = (int16_t)s1;
                         d.code = (d.sub == SUB_SWAP ? CODE_SWAP : CODE_MAT2) + pair_code(lo, hi);
+                    } else if (o.type == H_DENSE) {
+                        d.type = OP_DENSE;
+                        d.code = CODE_DENSE;
+                        d.sub = (uint32_t)tc_mode;
+                        // b = 1: U is unitary (no Kraus branch in the run), so the
+                        // kernel may restore each vector's norm after the product
+                        {
+                            double dev = 0;
+                            for (int r = 0; r < 32; ++r)
+                                for (int c2 = 0; c2 < 32; ++c2) {
+                                    cd acc = 0;
+                                    for (int k = 0; k < 32; ++k) acc += std::conj(o.du[32 * k + r]) * o.du[32 * k + c2];
+                                    dev = std::max(dev, std::abs(acc - (r == c2 ? 1.0 : 0.0)));
+                                }
+                            d.b = dev < 1e-9 ? 1 : 0;
+                        }
+                        d.mat = (uint32_t)(prog.mats.size() / 32);
+                        const size_t words = dense_b_words(tc_mode);
+                        // FP64 pool: U itself (2048 doubles), zero-padded to the slots
+                        // the FP32 B parts take
+                        for (size_t k = 0; k < words; ++k)
+                            prog.mats.push_back(k < 2048 ? ((k & 1) ? o.du[k / 2].imag() : o.du[k / 2].real()) : 0.0);
+                        std::vector<float> b(words);
+                        encode_dense_b(o.du.data(), tc_mode, b.data());
+                        prog.dense_b.emplace_back(d.mat, std::move(b));
+                        // the absorbed fixed-bit terms: a per-thread constant phase
+                        d.phi0 = to_fixed(o.phi0, false);
+                        d.term_begin = (uint32_t)prog.term_mask.size();
+                        d.csr[0] = 0;
+                        for (int mu = 1; mu <= 33; ++mu) d.csr[mu] = (uint16_t)o.terms.size();
+                        d.mu_mask = 0;
+                        for (auto &t : o.terms) {
+                            prog.term_mask.push_back(t.first);
+                            prog.term_phi.push_back(to_fixed(t.second, false));
+                        }
                     } else {
                         d.type = OP_DIAG;
                         d.code = CODE_DIAG;
@@ -671,6 +877,8 @@ struct Encoder {
                 }
                 sd.op_count = (uint32_t)(prog.ops.size() - sd.op_begin);
             }
+            for (uint32_t k = pd.op0; k < (uint32_t)prog.ops.size(); ++k)
+                if (prog.ops[k].type == OP_DENSE) pd.flags |= PF_DENSE;
             if (Kpass != cd(1.0, 0.0)) {
                 // the scalar goes on the first stage that multiplies by a
                 // per-thread phase anyway (it has a diagonal op), else on the last
@@ -688,7 +896,7 @@ struct Encoder {
             pd.nterm = (uint32_t)prog.term_mask.size() - pd.term0;
             pd.prog_bytes = pd.nops * (uint32_t)sizeof(DevOp) + pd.nmat * mat_bytes + pd.nterm * 16;
             // the kernels reserve exactly this much shared memory for a program
-            if (pd.prog_bytes > kMaxPassProgramBytes)
+            if (pd.prog_bytes > ((pd.flags & PF_DENSE) ? kMaxDensePassProgramBytes : kMaxPassProgramBytes))
                 throw std::logic_error("encoder: pass program exceeds the shared-memory budget");
             pass_ids.push_back((int)prog.passes.size());
             prog.passes.push_back(pd);
@@ -728,6 +936,7 @@ struct Compiler {
         L = std::min(lmax, n);
         enc.Lmax = L;
         enc.lookahead = co.schedule == 0;
+        enc.tc_mode = co.precision == TUSQ_C64 ? co.tc_mode : TUSQ_TC_NONE;
         // the lowest qubits stay in every window (contiguous 128-byte runs),
         // leaving room for any two-qubit gate
         int nf = std::min(co.precision == TUSQ_C128 ? 3 : 4, std::max(L - 2, 0));
@@ -1106,6 +1315,8 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
         if ((st.type == ST_RESTORE && (st.snap < 0 || st.snap >= top)) || (st.type == ST_CHECK && st.snap >= top))
             throw std::logic_error("compile: step snapshot slot out of range");
     prog.matsf.assign(prog.mats.begin(), prog.mats.end());
+    for (const auto &db : prog.dense_b)
+        std::copy(db.second.begin(), db.second.end(), prog.matsf.begin() + 32 * (size_t)db.first);
 }
 
 }  // namespace tusq

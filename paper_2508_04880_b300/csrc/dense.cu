@@ -10,12 +10,9 @@
 
 namespace tusq {
 
-size_t dense_b_words(int mode);
-void encode_dense_b(const std::complex<double> *u, int mode, float *out);
-
 template <int MODE>
 __global__ void __launch_bounds__(256, 1) dense_check_kernel(const float2 *x, float2 *y, const float *b,
-                                                             uint32_t b_bytes, unsigned int *err) {
+                                                             uint32_t b_bytes, unsigned int *err, int renorm) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
@@ -31,7 +28,7 @@ __global__ void __launch_bounds__(256, 1) dense_check_kernel(const float2 *x, fl
     for (int i = 0; i < 32; ++i) a[i] = x[32 * tid + i];
     dense_setup(&tmem_slot, &mbar, tid);
     DenseCtx c{tmem_slot, smem_u32(&mbar), 0u, err, &abort_flag, 0};
-    dense_apply<MODE>(a, abase, bbase, c, tid);
+    dense_apply<MODE>(a, abase, bbase, c, tid, renorm != 0);
 #pragma unroll
     for (int i = 0; i < 32; ++i) y[32 * tid + i] = a[i];
     dense_teardown(c.tmem, tid);
@@ -40,6 +37,7 @@ __global__ void __launch_bounds__(256, 1) dense_check_kernel(const float2 *x, fl
 template <int MODE>
 static cudaError_t launch_check(const float2 *x, float2 *y, const float *b, uint32_t bb, unsigned int *err,
                                 cudaStream_t st) {
+    const int renorm = 0;     // the diagnostic checks the raw tensor-core product
     // staging + B parts + 64 KiB of slack after them, so that a descriptor
     // read with the leading and stride offsets exchanged would still stay
     // inside this CTA's allocation
@@ -47,7 +45,7 @@ static cudaError_t launch_check(const float2 *x, float2 *y, const float *b, uint
     cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dense_check_kernel<MODE><<<1, 256, smem, st>>>(x, y, b, bb, err);
+    dense_check_kernel<MODE><<<1, 256, smem, st>>>(x, y, b, bb, err, renorm);
     return cudaGetLastError();
 }
 

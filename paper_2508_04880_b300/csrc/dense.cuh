@@ -90,7 +90,8 @@ struct DenseCtx {
 };
 
 // Wait for the mbarrier phase with a bound of ~1 s of SM clock; on timeout
-// set the error word and the CTA's abort flag and return false.
+// set the error word and the CTA's abort flag and return false.  Callers
+// read the abort flag only after a barrier that follows this wait.
 __device__ __forceinline__ bool dense_wait(DenseCtx &c) {
     const long long t0 = clock64();
     uint32_t done = 0;
@@ -155,19 +156,30 @@ __device__ __forceinline__ void dense_stage_row(const float2 (&a)[32], unsigned 
 // K = 64 product per split term into its own 64 TMEM columns.
 template <int MODE>
 __device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abase, const unsigned char *bbase,
-                                            DenseCtx &c, int tid) {
+                                            DenseCtx &c, int tid, bool renorm) {
     constexpr bool kBF = MODE == TUSQ_TC_BF16X3;
     constexpr uint32_t kApart = dense_a_part_bytes(MODE), kBpart = dense_b_part_bytes(MODE);
     constexpr int kSteps = kBF ? 4 : 8;            // K = 64 in steps of 16 (BF16) or 8 (TF32)
     const uint32_t a_s = smem_u32(abase), b_s = smem_u32(bbase);
     const int warp = tid >> 5;
+    // *c.abort only changes inside dense_wait, and every read of it follows
+    // the barrier after that wait, so all threads see the same value
+    if (*c.abort) return;
+    // |x|^2 of the thread's vector: a unitary U keeps it, and the tensor
+    // cores' FP32 accumulation shrinks it by a few units in the last place
+    // per product (a bias, not noise), so the result is scaled back to it
+    float nx = 0.f;
+    if (renorm) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) nx = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, nx));
+    }
     __syncthreads();                               // every thread has gathered its amplitudes
     for (int rd = 0; rd < 2; ++rd) {
         const bool mine = (tid >> 7) == rd;
         if (mine) dense_stage_row<MODE>(a, abase, tid & 127);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0 && !c.skip_issue && !*c.abort) {
+        if (tid == 0 && !c.skip_issue) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t idesc = dense_idesc(kBF);
             const uint32_t d = c.tmem + 64u * rd;
@@ -185,10 +197,9 @@ __device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abas
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
                          : "memory");
         }
-        if (*c.abort || !dense_wait(c)) {
-            __syncthreads();
-            return;
-        }
+        dense_wait(c);                             // on timeout: error word and abort flag
+        __syncthreads();
+        if (*c.abort) return;                      // uniform: read after the barrier
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (mine) {
             uint32_t r[64];
@@ -214,6 +225,14 @@ __device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abas
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 32; ++i) a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+            if (renorm) {
+                float ny = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) ny = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, ny));
+                const float sc = ny > 0.f ? sqrtf(nx / ny) : 1.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) a[i] = make_float2(a[i].x * sc, a[i].y * sc);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dense.cuh"
 #include "program.h"
 
 namespace tusq {
@@ -332,7 +333,7 @@ __device__ __forceinline__ SProg<R> load_program(const PassDesc &d, unsigned cha
 // tb); threads beyond 2^(L-V) only take part in the barriers.
 template <typename R, int V>
 __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const PassDesc &d, const SProg<R> &P,
-                                           int tid, uint64_t tb) {
+                                           int tid, uint64_t tb, DenseCtx *dc = nullptr) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
@@ -358,7 +359,28 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
             typename Phase<R>::U acc = 0;     // the stage's per-thread constant phase
             for (uint32_t k = 0; k < sd.op_count; ++k) {
                 const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
-                if (op.code != CODE_DIAG) {
+                if (op.code == CODE_DENSE) {
+                    // tensor cores: the stage's thread-independent run as one 32x32
+                    // matrix (every thread of the CTA takes part); its fixed-bit
+                    // terms join the per-thread constant phase
+                    if constexpr (sizeof(R) == 4 && V == 5) {
+                        if (op.csr[1] > op.csr[0] || op.phi0 != 0) {
+                            if (!have_gfix) {
+                                gfix = tb;
+                                for (int i = 0; i < L - V; ++i)
+                                    if (tid >> i & 1) gfix |= 1ull << sd.cglob[i];
+                                have_gfix = true;
+                            }
+                            apply_diag<R, V>(a, op, P, gfix, acc);
+                        }
+                        const unsigned char *bptr = reinterpret_cast<const unsigned char *>(P.mats + 16 * (op.mat - P.mat0));
+                        unsigned char *stg = reinterpret_cast<unsigned char *>(tile);
+                        const bool renorm = op.b != 0;    // U is unitary
+                        if (op.sub == TUSQ_TC_TF32X3) dense_apply<TUSQ_TC_TF32X3>(a, stg, bptr, *dc, tid, renorm);
+                        else if (op.sub == TUSQ_TC_BF16X3) dense_apply<TUSQ_TC_BF16X3>(a, stg, bptr, *dc, tid, renorm);
+                        else dense_apply<TUSQ_TC_TF32>(a, stg, bptr, *dc, tid, renorm);
+                    }
+                } else if (op.code != CODE_DIAG) {
                     apply_matrix_op<V, R>(a, op, P);
                 } else {
                     if (!have_gfix) {
@@ -429,6 +451,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     const float wleaf = (float)d.leaf_w;
     __syncthreads();
 
+    // tensor-core dense ops: 128 TMEM columns and a completion mbarrier
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_abort;
+    DenseCtx dctx{0u, 0u, 0u, args.err, &s_abort, args.dense_skip};
+    const bool dense = (flags & PF_DENSE) != 0;
+    // once a tensor-core wait of this traversal has run out, its later dense
+    // passes do nothing (the result is void and reported as a timeout)
+    if (dense && *args.err) return;
+    if (dense) {
+        if (tid == 0) s_abort = 0;
+        dense_setup(&s_tmem, &s_mbar, tid);
+        dctx.tmem = s_tmem;
+        dctx.mbar = smem_u32(&s_mbar);
+    }
+
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
 
     // tile bits of this CTA's first tile and of the grid stride, deposited
@@ -458,7 +496,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
-        run_stages<R, V>(tile, d, P, tid, tb);
+        run_stages<R, V>(tile, d, P, tid, tb, dense ? &dctx : nullptr);
+        if (dense && s_abort) break;     // a tensor-core wait ran out: stop (uniform after the stage barrier)
         // store + epilogue
         float pn = 0.f, pr = 0.f, pi = 0.f;
         double dn = 0.0, dr = 0.0, di = 0.0;
@@ -517,6 +556,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         }
         __syncthreads();
     }
+    if (dense) dense_teardown(dctx.tmem, tid);
     if (flags & PF_REDUCE) {
         // fixed-order block reduction: warp shuffles, then thread 0
         __shared__ double wsum[3][32];
@@ -618,8 +658,8 @@ static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
 }
 
 template <typename R, int V>
-static int occupancy_t(int L) {
-    const size_t smem = ((sizeof(R) * 2) << L) + kMaxPassProgramBytes;
+static int occupancy_t(int L, uint32_t prog_cap) {
+    const size_t smem = ((sizeof(R) * 2) << L) + prog_cap;
     const int threads = 1 << (L - V);
     int nb = 0;
     if (allow_smem<R, V>(smem) != cudaSuccess) return 1;
@@ -646,22 +686,24 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaS
     }
 }
 
-// Resident CTAs per SM for a pass configuration (for grid sizing).
-int pass_occupancy(int precision, int V, int L) {
+// Resident CTAs per SM for a pass configuration (for grid sizing); dense:
+// the pass carries tensor-core dense ops (larger program budget).
+int pass_occupancy(int precision, int V, int L, bool dense) {
+    const uint32_t cap = dense ? kMaxDensePassProgramBytes : kMaxPassProgramBytes;
     if (precision == TUSQ_C128) {
         switch (V) {
-        case 1: return occupancy_t<double, 1>(L);
-        case 2: return occupancy_t<double, 2>(L);
-        case 3: return occupancy_t<double, 3>(L);
-        default: return occupancy_t<double, 4>(L);
+        case 1: return occupancy_t<double, 1>(L, cap);
+        case 2: return occupancy_t<double, 2>(L, cap);
+        case 3: return occupancy_t<double, 3>(L, cap);
+        default: return occupancy_t<double, 4>(L, cap);
         }
     }
     switch (V) {
-    case 1: return occupancy_t<float, 1>(L);
-    case 2: return occupancy_t<float, 2>(L);
-    case 3: return occupancy_t<float, 3>(L);
-    case 4: return occupancy_t<float, 4>(L);
-    default: return occupancy_t<float, 5>(L);
+    case 1: return occupancy_t<float, 1>(L, cap);
+    case 2: return occupancy_t<float, 2>(L, cap);
+    case 3: return occupancy_t<float, 3>(L, cap);
+    case 4: return occupancy_t<float, 4>(L, cap);
+    default: return occupancy_t<float, 5>(L, cap);
     }
 }
 

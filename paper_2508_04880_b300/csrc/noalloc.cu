@@ -25,7 +25,7 @@
 namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
 cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st);
-int pass_occupancy(int precision, int V, int L);
+int pass_occupancy(int precision, int V, int L, bool dense);
 cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
                             int is_check, double *drift_log, int check, int *restore_flag,
@@ -187,7 +187,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
         for (size_t i = 0; i < pg.passes.size(); ++i) {
             const PassDesc &d = pg.passes[i];
             int V = std::min(pg.reg_bits, d.L);
-            if (!occ[d.L]) occ[d.L] = pass_occupancy(o.precision, V, d.L);
+            if (!occ[d.L]) occ[d.L] = pass_occupancy(o.precision, V, d.L, false);
             uint64_t g = std::min<uint64_t>(d.ntiles, (uint64_t)nsm * occ[d.L]);
             grid[i] = (int)std::max<uint64_t>(g, 1);
             max_grid = std::max(max_grid, grid[i]);
@@ -241,6 +241,8 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
             a.matsf = (const float *)at(lay.matsf);
             a.tmask = (const uint64_t *)at(lay.tmask);
             a.tphi = (const uint64_t *)at(lay.tphi);
+            a.err = nullptr;          // no dense ops here (tc_mode is not used), so nothing waits
+            a.dense_skip = 0;
             last_grid = grid[s.pass];
             NA_TRY(launch_pass(a, o.precision, std::min(pg.reg_bits, a.d.L), last_grid, st));
             break;

@@ -2,7 +2,9 @@
 // compiler (host C++) and the CUDA kernels/runtime.
 #pragma once
 
+#include <complex>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include "../../include/tusq.h"
@@ -14,7 +16,7 @@ constexpr int kMaxStages = 8;        // register stages per pass
 constexpr int kRegBitsC64 = 5;       // amplitudes per thread = 2^5 (complex64)
 constexpr int kRegBitsC128 = 4;      // 2^4 (complex128)
 
-enum DevOpType : int32_t { OP_MAT1 = 1, OP_MAT2 = 2, OP_DIAG = 3 };
+enum DevOpType : int32_t { OP_MAT1 = 1, OP_MAT2 = 2, OP_DIAG = 3, OP_DENSE = 4 };
 
 // Structure of a matrix op (DevOp::sub), chosen on the host so the kernel
 // spends fewer FMAs.  MAT1: general; real entries; and the RX-type form
@@ -70,7 +72,26 @@ static_assert(sizeof(DevOp) % 16 == 0, "DevOp alignment");
 // (CODE_PROD + sub) is a run of 2x2s of one form on distinct register bits:
 // `a` is the mask of those bits and bit b's matrix is entries 4b..4b+3 of
 // the two matrix slots starting at `mat`.
-enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DIAG = 64, CODE_PROD = 80 };
+enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DIAG = 64, CODE_PROD = 80,
+                          CODE_DENSE = 96 };
+
+// Tensor-core dense op (OP_DENSE, code CODE_DENSE, sub = the tc mode): the
+// stage's 32 registers times one 32x32 complex matrix U.  `mat` is its first
+// matrix slot: the FP32 pool holds the B operand parts of U in the kernels'
+// shared-memory layout (dense_b_words(mode) words), the FP64 pool holds U
+// itself (row-major, 2048 doubles) for host-side interpreters.  phi0 and the
+// csr[0]..csr[1] terms are diagonal terms on fixed bits only: a per-thread
+// constant phase (mu_mask is 0).  b = 1 when U is unitary: each thread's
+// 32-vector then keeps its norm, which the kernel restores after the
+// tensor-core product.  Only 13-qubit complex64 tiles (256 threads, V = 5)
+// carry dense ops.
+constexpr int kDenseTileBits = 13;
+constexpr double kDenseMinCost = 24.0;   // SIMT instructions per amplitude a run must cost
+
+// FP32 words of the B operand parts of one dense op, and their encoding from
+// U (row-major 32x32 complex) into the kernels' layout.
+size_t dense_b_words(int mode);
+void encode_dense_b(const std::complex<double> *u, int mode, float *out);
 
 TUSQ_HD constexpr uint32_t pair_code(int lo, int hi) {
     return (uint32_t)(lo * (9 - lo) / 2 + (hi - lo - 1));
@@ -97,12 +118,16 @@ struct StageDesc {
 constexpr int kMaxStageOps = 48;
 constexpr int kMaxDiagTerms = 256;
 constexpr uint32_t kMaxPassProgramBytes = 40 * 1024;
+// A pass with tensor-core dense ops carries their B operands (16 or 32 KiB
+// each) in its program: it may use up to this much (one CTA per SM then).
+constexpr uint32_t kMaxDensePassProgramBytes = 160 * 1024;
 
 enum PassFlags : uint32_t {
     PF_WRITE = 1,          // write the tile back to the state
     PF_SNAPSHOT = 2,       // also write it to the snapshot buffer
     PF_LEAF = 4,           // acc[x] += w |psi_x|^2
     PF_REDUCE = 8,         // partial sums of |psi|^2 and sum h(x) psi_x
+    PF_DENSE = 16,         // has tensor-core dense ops (TMEM is allocated)
 };
 
 struct PassDesc {
@@ -154,6 +179,9 @@ struct Program {
     std::vector<DevOp> ops;
     std::vector<double> mats;        // 32 doubles (16 complex) per matrix slot
     std::vector<float> matsf;        // the same slots in FP32 (complex64 kernels)
+    // dense ops: (first slot, FP32 words) written over matsf after the
+    // FP64 -> FP32 conversion of the pool
+    std::vector<std::pair<uint32_t, std::vector<float>>> dense_b;
     std::vector<uint64_t> term_mask;
     std::vector<uint64_t> term_phi;
     int max_depth = 0;
@@ -180,6 +208,9 @@ struct PassArgs {
     const float *matsf;
     const uint64_t *tmask;
     const uint64_t *tphi;
+    unsigned int *err;    // bit 0 set when a bounded device wait ran out
+    int dense_skip;       // test hook: dense ops never issue their tensor-core work
+    int pad;
 };
 
 // One job of a batch launch: its steps in the batch's step array (pass,
@@ -226,6 +257,7 @@ struct CompileOpts {
     int snapshots;         // snapshot slots available for branch nodes
     int schedule;          // 0 lookahead window growth, 1 list order
     int cache_states = 0;  // DFTT+Caching capacity; < 0: one per layer, at most kDefaultCacheStates
+    int tc_mode = TUSQ_TC_NONE;  // tensor-core dense stages (complex64 only)
 };
 
 constexpr int kDefaultCacheStates = 8;

@@ -16,7 +16,7 @@ namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
 
 cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st);
-int pass_occupancy(int precision, int V, int L);
+int pass_occupancy(int precision, int V, int L, bool dense);
 cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
                             int is_check, double *drift_log, int check, int *restore_flag,
@@ -56,6 +56,7 @@ struct tusq_exec {
     std::vector<int> grid_of_pass;
     int max_grid = 1;
     double record_bias = 0.0;
+    int dense_skip = 0;             // test hook: dense ops do not issue (their waits run out)
     uint64_t launches = 0;
     size_t footprint = 0;
     bool profiling = false;
@@ -132,6 +133,7 @@ static CompileOpts compile_opts_of(const tusq_run_opts *o, size_t state_bytes) {
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
     co.cache_states = o->cache_states;
+    co.tc_mode = o->tc_mode;
     return co;
 }
 
@@ -173,7 +175,9 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
             info->stages += d.n_stages;
             info->diag_terms += d.nterm;
             for (uint32_t k = 0; k < d.nops; ++k) {
-                if (pg.ops[d.op0 + k].type == OP_DIAG) info->diag_ops++;
+                const int t = pg.ops[d.op0 + k].type;
+                if (t == OP_DIAG) info->diag_ops++;
+                else if (t == OP_DENSE) info->dense_ops++;
                 else info->matrix_ops++;
             }
         } else if (s.type == ST_INIT) {
@@ -287,7 +291,7 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     if (k_parts < 0) {
         const int L = tile_bits(p->n, o);
         const int V = std::min(o->precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, L);
-        k_parts = auto_subtrees(p->n, o, (uint64_t)e->nsm * pass_occupancy(o->precision, V, L));
+        k_parts = auto_subtrees(p->n, o, (uint64_t)e->nsm * pass_occupancy(o->precision, V, L, false));
     }
     if (k_parts > 1 && p->n_inst() >= 2) {
         const int rc = create_parts(e, p, o, k_parts);
@@ -317,8 +321,9 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
     for (size_t i = 0; i < pg.passes.size(); ++i) {
         const PassDesc &d = pg.passes[i];
         int V = std::min(e->V, d.L);
-        int &occ = occ_cache[0][d.L];
-        if (!occ) occ = pass_occupancy(o->precision, V, d.L);
+        const bool dense = (d.flags & PF_DENSE) != 0;
+        int &occ = occ_cache[dense ? 1 : 0][d.L];
+        if (!occ) occ = pass_occupancy(o->precision, V, d.L, dense);
         uint64_t g = std::min<uint64_t>(d.ntiles, (uint64_t)e->nsm * occ);
         e->grid_of_pass[i] = (int)std::max<uint64_t>(g, 1);
         e->max_grid = std::max(e->max_grid, e->grid_of_pass[i]);
@@ -430,6 +435,8 @@ static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
             a.matsf = e->matsf;
             a.tmask = e->tmask;
             a.tphi = e->tphi;
+            a.err = reinterpret_cast<unsigned int *>(e->counters + 3);
+            a.dense_skip = e->dense_skip;
             last_grid = e->grid_of_pass[s.pass];
             if (e->profiling) CUDA_TRY(cudaEventRecord(e->prof_ev[2 * npass], st));
             CUDA_TRY(launch_pass(a, e->opts.precision, std::min(e->V, a.d.L), last_grid, st));
@@ -522,6 +529,10 @@ int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
         info->unrecovered = cnt[1];
         info->kernel_launches = e->launches;
         info->max_drift = maxd;
+    }
+    if (cnt[3]) {
+        set_error("a bounded device wait for the tensor cores ran out; the traversal stopped early");
+        return TUSQ_ETIMEOUT;
     }
     if (cnt[1]) {
         set_error("drift above tolerance at a branch node without a snapshot");
@@ -672,6 +683,13 @@ int tusq_exec_finish(tusq_exec *e, tusq_run_info_t *info) {
     return exec_finish(e, info);
 }
 
+int tusq_exec_set_dense_skip(tusq_exec *e, int on) {
+    if (!e) { set_error("tusq_exec_set_dense_skip: NULL exec"); return TUSQ_EINVAL; }
+    e->dense_skip = on != 0;
+    for (tusq_exec *q : e->parts) q->dense_skip = on != 0;
+    return TUSQ_OK;
+}
+
 int tusq_exec_set_profiling(tusq_exec *e, int on) {
     if (!e) { set_error("tusq_exec_set_profiling: NULL exec"); return TUSQ_EINVAL; }
     e->profiling = on != 0;
@@ -688,7 +706,7 @@ int tusq_exec_pass_structure(tusq_exec *e, uint64_t *n_passes, const int32_t **f
             int32_t f[8] = {d.n_stages, (int32_t)d.nops, 0, 0, 0, (int32_t)d.nterm, (int32_t)d.flags, d.L};
             for (uint32_t k = 0; k < d.nops; ++k) {
                 int t = pg.ops[d.op0 + k].type;
-                f[t == OP_MAT1 ? 2 : t == OP_MAT2 ? 3 : 4]++;
+                f[t == OP_MAT1 ? 2 : (t == OP_MAT2 || t == OP_DENSE) ? 3 : 4]++;
             }
             e->structure.insert(e->structure.end(), f, f + 8);
         }

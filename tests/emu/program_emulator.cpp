@@ -10,7 +10,8 @@
 // oracle without a GPU.  The diagonal runs are evaluated both from the
 // per-register fixed-point angles (a Walsh-Hadamard form of the register-mask
 // groups whose phases the kernels apply group by group) and directly from the
-// global index; any mismatch is reported.
+// global index; any mismatch is reported.  Tensor-core dense ops apply the
+// FP64 matrix U the compiler stored beside their B operand parts.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -99,7 +100,16 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                             }
                         }
                     };
-                    if (op.type == OP_MAT1 && op.code >= CODE_PROD) {
+                    if (op.type == OP_DENSE) {
+                        // U from the FP64 pool (row-major 32x32); its absorbed
+                        // fixed-bit terms follow as a per-thread constant phase
+                        std::vector<cd> y(1 << v, cd(0));
+                        for (int r = 0; r < (1 << v); ++r)
+                            for (int c2 = 0; c2 < (1 << v); ++c2) y[r] += M(32 * r + c2) * a[c2];
+                        a = y;
+                    }
+                    if (op.type == OP_DENSE && op.csr[1] == op.csr[0] && op.phi0 == 0) {
+                    } else if (op.type == OP_MAT1 && op.code >= CODE_PROD) {
                         // product op: bit b's 2x2 at matrix entries 4b..4b+3
                         for (int bit = 0; bit < v; ++bit)
                             if (op.a >> bit & 1) two_by_two(bit, 4 * bit);
@@ -192,6 +202,7 @@ extern "C" int emu_run(const tusq_plan_t *p, const tusq_run_opts *o, double *pro
     bool snaps = co.checks || o->traversal == TUSQ_DFTT_SNAPSHOT;
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
     co.cache_states = o->cache_states;
+    co.tc_mode = o->tc_mode;
     Program pg;
     compile_program(*p, co, pg);
     const uint64_t dim = 1ULL << p->n;

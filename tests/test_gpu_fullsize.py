@@ -17,7 +17,8 @@ element by element (max-abs 1e-5, total variation 1e-4).  The whole
 20-qubit brickwork, depth 40 (Haar SU(2) on every qubit and CZ on
 alternating neighbour pairs, 1180 gates), 1q/2q depolarizing 1e-3/1e-2, 1e6
 shots, pruned: the whole 101-leaf plan against the oracle, in complex64
-(1e-5 / 1e-4) and in the complex128 mode (1e-12 / 1e-10).
+(1e-5 / 1e-4; SIMT and the two split tensor-core modes) and in the
+complex128 mode (1e-12 / 1e-10).
 
 The largest state the serving mix admits (30 qubits, 8 GiB) is checked
 against a closed form: a GHZ circuit under Pauli noise, whose every instance
@@ -148,6 +149,19 @@ def test_brickwork20_depth40_all_leaves_c64(brickwork20, trav):
     probs, info = _run(pl, precision=T.C64, traversal=trav)
     _compare(probs, ref, MAX_ABS, TV, f"20q brickwork depth 40, complex64, traversal {trav}")
     assert info["leaf_passes"] == 101 and info["unrecovered"] == 0
+
+
+@pytest.mark.parametrize("tc_mode", [T.TC_TF32X3, T.TC_BF16X3])
+def test_brickwork20_depth40_all_leaves_tensor_cores(brickwork20, tc_mode):
+    # the single-qubit layers of most register stages as 32x32 matrices on
+    # the tensor cores (split TF32 or BF16 products, FP32 accumulation, the
+    # norm of each unitary stage's vectors restored): same tolerance as the
+    # SIMT path
+    circ, opl, ref = brickwork20
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), _events(opl.inst), opl.weights)
+    probs, info = _run(pl, precision=T.C64, traversal=T.DFTT_SNAPSHOT, tc_mode=tc_mode)
+    _compare(probs, ref, MAX_ABS, TV, f"20q brickwork depth 40, tensor cores mode {tc_mode}")
+    assert info["dense_ops"] > 0 and info["leaf_passes"] == 101
 
 
 def test_brickwork20_depth40_all_leaves_c128(brickwork20):

@@ -25,7 +25,7 @@ def emu():
     global _emu
     if _emu is None:
         srcs = [os.path.join(HERE, "emu", "program_emulator.cpp")] + \
-            [os.path.join(CSRC, f) for f in ("compile.cpp", "plan.cpp", "capi.cpp")]
+            [os.path.join(CSRC, f) for f in ("compile.cpp", "plan.cpp", "capi.cpp", "dense_host.cpp")]
         deps = srcs + [os.path.join(CSRC, f) for f in ("program.h", "internal.h")]
         if not os.path.exists(SO) or any(os.path.getmtime(d) > os.path.getmtime(SO) for d in deps):
             os.makedirs(os.path.dirname(SO), exist_ok=True)
@@ -113,3 +113,23 @@ def test_uncompute_without_drift_checks(leaf_peek, window):
     got, _ = emu_run(T.plan(circ, 5000, 3), precision=T.C128, traversal=T.DFTT, drift_tol=-1.0,
                      leaf_peek=leaf_peek, max_window=window)
     assert np.abs(got - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("tc_mode", [T.TC_TF32X3, T.TC_BF16X3])
+def test_tensor_core_dense_stages(tc_mode):
+    # with tc_mode, thread-independent runs of a register stage become one
+    # 32x32 matrix (Sec. II, Eq. 1); the interpreter applies the FP64 matrix
+    # the compiler stored, so the program's structure -- which ops were
+    # absorbed, the fixed-bit phases riding along, the pass split under the
+    # larger program budget -- is checked against the oracle
+    for circ, shots in [(W.brickwork(14, 8, 2, 2e-3, 2e-2), 20_000),
+                        (W.qaoa_3regular(14, 3, 4, 1e-3, 1e-2), 20_000)]:
+        ref, _ = oracle.run(circ, shots, 1)
+        pl = T.plan(circ, shots, 1)
+        for trav in TRAV:
+            st = T.tusq_compile_stats(pl, T.run_opts(precision=T.C64, traversal=trav, tc_mode=tc_mode))
+            got, info = emu_run(pl, precision=T.C64, traversal=trav, tc_mode=tc_mode)
+            assert info["diag_mismatch"] < 1e-9
+            assert np.abs(got - ref).max() < TOL[T.C64], (circ.name, trav)
+            if circ.name.startswith("brickwork"):
+                assert st["dense_ops"] > 0

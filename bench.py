@@ -296,7 +296,8 @@ def run_batch(args, T, torch):
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
         exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT,
-                                                                       use_graph=int(args.graph)),
+                                                                       use_graph=int(args.graph),
+                                                                       tc_mode=args.tc_mode),
                                               side[ki[0] % len(side)].cuda_stream), enumerate(large)))
 
     def step():
@@ -334,6 +335,7 @@ def run_batch(args, T, torch):
                    "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
                    "max_job_instances": args.max_job_instances,
                    "jobs_in_one_launch": len(small),
+                   "tc_mode_per_launch_jobs": ["none", "tf32x3", "bf16x3", "tf32"][args.tc_mode],
                    "jobs_on_streams": len(large), "instances": n_inst,
                    "autotuned": {"traversal": best.traversal, "schedule": best.schedule, "ms": tune_ms}},
         "plan_seconds": plan_s, "error_vs_oracle": errs,
@@ -575,6 +577,9 @@ def main():
     ap.add_argument("--slots", type=int, default=8,
                     help="served: stream slots of the serving loop (32 measured no higher capacity and a "
                          "higher p99 under load than 8)")
+    ap.add_argument("--tc-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="tensor-core dense stages: 0 none, 1 TF32x3, 2 BF16x3, 3 TF32 (main: the timed "
+                         "traversal; batch: the jobs run per launch)")
     ap.add_argument("--subtrees", type=int, default=1,
                     help="main: traverse the DFS order as this many concurrent chunks (parallel subtrees)")
     ap.add_argument("--graph", type=int, default=1,
@@ -630,7 +635,8 @@ def main():
     stream = torch.cuda.Stream() if args.graph else torch.cuda.current_stream()
     torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
-    opts = T.run_opts(precision=prec, traversal=trav, use_graph=int(args.graph), subtrees=args.subtrees)
+    opts = T.run_opts(precision=prec, traversal=trav, use_graph=int(args.graph), subtrees=args.subtrees,
+                      tc_mode=args.tc_mode)
     ex = T.Exec(plan, opts, sp)
     probs = torch.empty(1 << n, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
@@ -731,6 +737,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload], "qubits": n, "gates": circ.n_gates,
                    "shots": shots, "instances": n_inst, "traversal": args.traversal, "subtrees": args.subtrees,
+                   "tc_mode": ["none", "tf32x3", "bf16x3", "tf32"][args.tc_mode],
                    "l2": "inputs larger than L2 (state and output 2^n x 8 B each)",
                    "parallelism": f"replica x{world}"},
         "gate_amp_updates_per_s": (info["gate_apps"] + info["pauli_apps"]) * amps * world / secs,
@@ -753,9 +760,9 @@ def main():
     # plain GPU form (every instance from |0..0>) beside the headline
     # traversal, each timed over two traversals after one warm-up, with the
     # same kernels
-    arms = [("snapshot", T.run_opts(precision=prec, traversal=T.DFTT_SNAPSHOT)),
-            ("dftt_uncompute", T.run_opts(precision=prec, traversal=T.DFTT, drift_tol=1e-6)),
-            ("from_scratch", T.run_opts(precision=prec, traversal=T.FROM_SCRATCH))]
+    arms = [("snapshot", T.run_opts(precision=prec, traversal=T.DFTT_SNAPSHOT, tc_mode=args.tc_mode)),
+            ("dftt_uncompute", T.run_opts(precision=prec, traversal=T.DFTT, drift_tol=1e-6, tc_mode=args.tc_mode)),
+            ("from_scratch", T.run_opts(precision=prec, traversal=T.FROM_SCRATCH, tc_mode=args.tc_mode))]
     if not args.no_compare and rank == 0:
         other = {}
         for name, o in arms:
@@ -773,7 +780,7 @@ def main():
                            "checks": inf3["checks"], "instances_per_s": n_inst / (t3 / 1e3)}
             del e3
         line["traversals"] = other
-    if not args.no_error and rank == 0 and args.workload.startswith("qaoa"):
+    if not args.no_error and rank == 0:
         line["error_vs_oracle"] = error_vs_oracle(T, torch, circ, shots, seed, arms, sp)
     if not args.no_served and rank == 0:
         line["served"] = served_subrun(args, T, torch)

@@ -464,7 +464,11 @@ int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts, double *pr
 /* A serving loop that admits jobs while their device footprint
  * (state + accumulator + snapshots) fits hbm_budget_bytes, runs admitted
  * jobs concurrently on `n_streams` CUDA streams of the current device and
- * records each job's latency (submit to completion). */
+ * records each job's latency (submit to completion).  A pool of host threads
+ * compiles each job's device program as soon as it is submitted; one
+ * admission thread retires finished jobs and admits compiled ones in
+ * submission order (a compiled job that does not fit the budget is not
+ * overtaken). */
 int tusq_server_create(size_t hbm_budget_bytes, int n_streams, tusq_server **out);
 
 /* Queue a job; the plan must stay alive until the job completes.  probs_dev
@@ -475,6 +479,13 @@ int tusq_submit(tusq_server *s, const tusq_plan_t *p, const tusq_run_opts *opts,
 
 /* Non-blocking: *done = 1 once finished (latency_s then set). */
 int tusq_poll(tusq_server *s, uint64_t job_id, int *done, double *latency_s);
+
+/* Device-time interval of a finished job's traversal: the CUDA events
+ * recorded on its stream just before its first kernel and just after its
+ * last, in ms since the server was created (comparable between jobs, e.g.
+ * to see that admitted jobs ran concurrently).  TUSQ_EBUSY while the job
+ * runs; the job's own status once it is done. */
+int tusq_poll_device_interval(tusq_server *s, uint64_t job_id, double *start_ms, double *end_ms);
 
 /* Block until every submitted job is done. */
 int tusq_server_drain(tusq_server *s);

@@ -39,7 +39,7 @@ EXPORTS = [
     "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
     "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
-    "tusq_server_drain",
+    "tusq_poll_device_interval", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
 
@@ -136,6 +136,7 @@ def _load():
         "tusq_server_create": (i32, [ctypes.c_size_t, i32, P(vp)]),
         "tusq_submit": (i32, [vp, vp, P(RunOpts), vp, P(u64)]),
         "tusq_poll": (i32, [vp, u64, P(i32), P(f64)]),
+        "tusq_poll_device_interval": (i32, [vp, u64, P(f64), P(f64)]),
         "tusq_server_drain": (i32, [vp]),
         "tusq_server_free": (None, [vp]),
         "tusq_last_error": (ctypes.c_char_p, []),
@@ -508,6 +509,13 @@ class Server:
         lat = ctypes.c_double()
         _check(lib.tusq_poll(self.h, job_id, ctypes.byref(done), ctypes.byref(lat)))
         return bool(done.value), lat.value
+
+    def device_interval(self, job_id: int):
+        """(start_ms, end_ms) of a finished job's traversal on the device, in ms
+        since the server was created."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib.tusq_poll_device_interval(self.h, job_id, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def drain(self) -> None:
         _check(lib.tusq_server_drain(self.h))

@@ -57,6 +57,10 @@ struct tusq_exec {
     int max_grid = 1;
     double record_bias = 0.0;
     int dense_skip = 0;             // test hook: dense ops do not issue (their waits run out)
+    // prepared on the host, not yet materialised on the device: parallel
+    // subtrees still to cut from `plan` (0: none)
+    int pending_parts = 0;
+    const tusq_plan_t *plan = nullptr;
     uint64_t launches = 0;
     size_t footprint = 0;
     bool profiling = false;
@@ -209,9 +213,21 @@ static int auto_subtrees(int n, const tusq_run_opts *o, uint64_t slots) {
     return (int)std::min<uint64_t>(std::max<uint64_t>(k, 1), 16);
 }
 
-// Parallel subtrees: the plan's DFS order cut into k chunks (tusq_plan_shard),
-// one exec per chunk on its own non-blocking stream, an FP64 output per
-// chunk after the first.
+// Chunks a traversal is cut into: o->subtrees, or for -1 the automatic rule
+// with the current device's SM count and the pass kernel's CTAs per SM.
+// exec_footprint and exec_prepare both use it, so that a job admitted by its
+// footprint creates no more chunks than it paid for.
+static int chunk_count(const tusq_plan_t *p, const tusq_run_opts *o) {
+    if (o->subtrees >= 0) return o->subtrees;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+    const int L = tile_bits(p->n, o);
+    const int V = std::min(o->precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, L);
+    return auto_subtrees(p->n, o, (uint64_t)nsm * pass_occupancy(o->precision, V, L, false));
+}
+
 // Device bytes an exec of this plan needs (state + snapshots + program).
 size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
     size_t amp = o->precision == TUSQ_C128 ? 16 : 8;
@@ -222,8 +238,7 @@ size_t exec_footprint(const tusq_plan_t *p, const tusq_run_opts *o) {
         K = co.cache_states < 0 ? (int)std::min<uint64_t>(p->stats.n_noninv_layers, kDefaultCacheStates)
                                 : co.cache_states;
     const size_t one = state * (1 + co.snapshots + K) + (1u << 20);
-    // (auto: the same rule with 148 SMs and the launch bounds' CTAs per SM)
-    const int k = o->subtrees < 0 ? auto_subtrees(p->n, o, o->precision == TUSQ_C128 ? 148 : 296) : o->subtrees;
+    const int k = chunk_count(p, o);
     const uint64_t parts = k > 1 ? std::min<uint64_t>((uint64_t)k, std::max<uint64_t>(p->n_inst(), 1)) : 1;
     return one * parts + (parts - 1) * sizeof(double) * ((size_t)1 << p->n);
 }
@@ -245,6 +260,9 @@ int compile_stats(const tusq_plan_t *p, const tusq_run_opts *o, tusq_run_info_t 
 int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out);
 void exec_free(tusq_exec *e);
 
+// Parallel subtrees: the plan's DFS order cut into k chunks (tusq_plan_shard),
+// one exec per chunk on its own non-blocking stream, an FP64 output per
+// chunk after the first.
 static int create_parts(tusq_exec *e, const tusq_plan_t *p, const tusq_run_opts *o, int k_req) {
     const int k = (int)std::min<uint64_t>((uint64_t)k_req, p->n_inst());
     tusq_run_opts so = *o;
@@ -275,30 +293,25 @@ static int create_parts(tusq_exec *e, const tusq_plan_t *p, const tusq_run_opts 
     return TUSQ_OK;
 }
 
-int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out) {
+// Host half of creating an exec: the schedule compile and the grid of every
+// pass.  No device memory is touched (only device attributes are read), so
+// it can run on any host thread ahead of admission.
+int exec_prepare(const tusq_plan_t *p, const tusq_run_opts *o, tusq_exec **out) {
     tusq_exec *e = new (std::nothrow) tusq_exec;
     if (!e) { set_error("tusq_exec_create: out of host memory"); return TUSQ_ENOMEM; }
     e->opts = *o;
     e->n = p->n;
     e->dim = 1ULL << p->n;
     e->amp_bytes = o->precision == TUSQ_C128 ? 16 : 8;
-    e->stream = st;
+    e->plan = p;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e->nsm <= 0) e->nsm = 148;
-    int k_parts = o->subtrees;
-    if (k_parts < 0) {
-        const int L = tile_bits(p->n, o);
-        const int V = std::min(o->precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, L);
-        k_parts = auto_subtrees(p->n, o, (uint64_t)e->nsm * pass_occupancy(o->precision, V, L, false));
-    }
+    const int k_parts = chunk_count(p, o);
     if (k_parts > 1 && p->n_inst() >= 2) {
-        const int rc = create_parts(e, p, o, k_parts);
-        if (rc != TUSQ_OK) {
-            exec_free(e);
-            return rc;
-        }
+        // the chunks are cut and compiled when the exec is materialised
+        e->pending_parts = k_parts;
         *out = e;
         return TUSQ_OK;
     }
@@ -328,6 +341,23 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
         e->grid_of_pass[i] = (int)std::max<uint64_t>(g, 1);
         e->max_grid = std::max(e->max_grid, e->grid_of_pass[i]);
     }
+    e->footprint = state_bytes * (1 + e->n_snaps);
+    *out = e;
+    return TUSQ_OK;
+}
+
+// Device half: allocate the state, snapshots, records and program buffers on
+// stream st and upload the program.  On failure the exec is freed.
+int exec_materialize(tusq_exec *e, cudaStream_t st) {
+    e->stream = st;
+    if (e->pending_parts) {
+        const int rc = create_parts(e, e->plan, &e->opts, e->pending_parts);
+        e->pending_parts = 0;
+        if (rc != TUSQ_OK) exec_free(e);
+        return rc;
+    }
+    Program &pg = e->prog;
+    const size_t state_bytes = e->amp_bytes * e->dim;
     int rc;
 #define ALLOC(ptr, bytes) \
     if ((rc = dmalloc(&(ptr), (bytes), st)) != TUSQ_OK) { release(e); delete e; return rc; }
@@ -359,15 +389,18 @@ int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, t
         delete e;
         return rc;
     }
-    // the host program arrays are consumed by the asynchronous copies
-    cudaError_t ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) {
-        release(e);
-        delete e;
-        set_error(std::string("tusq_exec_create: ") + cudaGetErrorString(ce));
-        return TUSQ_ECUDA;
-    }
-    e->footprint = state_bytes * (1 + e->n_snaps);
+    // the program's host arrays live as long as the exec, so the copies need
+    // no wait here; errors of the queued work surface at the next
+    // synchronisation (tusq_exec_finish)
+    return TUSQ_OK;
+}
+
+int exec_create(const tusq_plan_t *p, const tusq_run_opts *o, cudaStream_t st, tusq_exec **out) {
+    tusq_exec *e = nullptr;
+    int rc = exec_prepare(p, o, &e);
+    if (rc != TUSQ_OK) return rc;
+    rc = exec_materialize(e, st);
+    if (rc != TUSQ_OK) return rc;
     *out = e;
     return TUSQ_OK;
 }
@@ -593,8 +626,10 @@ void exec_free(tusq_exec *e) {
     if (e->fork_ev) cudaEventDestroy(e->fork_ev);
     for (cudaEvent_t ev : e->join_ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : e->prof_ev) cudaEventDestroy(ev);
+    const bool on_device = e->state || !e->parts.empty();
     release(e);
-    cudaStreamSynchronize(e->stream);
+    // a prepared exec that never reached the device has nothing queued
+    if (on_device) cudaStreamSynchronize(e->stream);
     delete e;
 }
 

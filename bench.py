@@ -684,6 +684,13 @@ def main():
                 "mean_launch_ms": float(pms.mean()) if len(pms) else 0.0,
                 "algorithmic_bytes_per_launch": per_launch_bytes}
 
+    # measured FP32 / FP64 FMA peaks of this device (own kernels), with the
+    # SM clock sampled meanwhile: the denominators of the SIMT rooflines
+    with ClockSampler(local) as clk_alu:
+        fp32_tf, fp64_tf = T.tusq_measure_alu_peaks(sp)
+    alu_peaks = {"fp32_tflops": fp32_tf, "fp64_tflops": fp64_tf, "clocks": clk_alu.summary(),
+                 "how": "FMA chains, 8 CTAs x 256 threads per SM, best of 3 timed launches (CUDA events)"}
+
     # shot sampling of the output (1e6 shots): integer prefix sum over the
     # 2^n outcomes, then one Philox draw and binary search per shot
     counts = torch.empty(1 << n, dtype=torch.uint64, device="cuda")
@@ -750,6 +757,7 @@ def main():
                 "sum_probs": total},
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
         "sample": sample_info,
+        "alu_peaks": alu_peaks,
         "run_info": {k: info[k] for k in ("passes", "gate_apps", "pauli_apps", "leaf_passes", "checks",
                                           "restores", "unrecovered", "resets", "max_drift")},
         "plan": {k: pst[k] for k in ("n_raw_unique", "n_commuted_unique", "n_instances",

@@ -378,6 +378,14 @@ int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
 int tusq_dense_check(int tc_mode, const double *u_host, const float *x_dev, float *y_dev,
                      void *cuda_stream);
 
+/* Measured FP32 and FP64 fused multiply-add throughput of the current
+ * device (TFLOP/s, 2 flops per FMA): the peaks the rooflines of the SIMT
+ * pass kernels are stated against.  Own kernels (eight independent FMA
+ * chains per thread, 8 CTAs of 256 threads per SM), best of three timed
+ * launches after a warm-up, CUDA events on cuda_stream; takes well under a
+ * second.  The SM clock during the call is the caller's to sample. */
+int tusq_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops, void *cuda_stream);
+
 /* ------------------------------------------------------- shot sampling */
 
 /* Shots drawn from an output distribution on the device.  The paper samples
@@ -453,6 +461,9 @@ int tusq_batch_autotune(const tusq_plan_t *const *plans, uint32_t n_jobs, const 
  * the last call's contents (what must start at zero is cleared on entry):
  * calls whose work overlaps on the GPU race with each other.  The call
  * synchronises `cuda_stream` before returning and fills *info if given.
+ * Options are range-checked as by tusq_run; subtrees, use_graph, cache_states
+ * and tc_mode are then ignored (one traversal, direct launches, no
+ * DFTT+Caching cache, SIMT stages).
  * Errors: TUSQ_EINVAL with a message when the state (more than half the
  * scratch) or state + program do not fit -- use tusq_run then; TUSQ_ECUDA,
  * TUSQ_EDRIFT as tusq_run. */

@@ -37,7 +37,7 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
-    "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
+    "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_measure_alu_peaks", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_poll_device_interval", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
@@ -127,6 +127,7 @@ def _load():
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
         "tusq_dense_check": (i32, [i32, P(f64), vp, vp, vp]),
+        "tusq_measure_alu_peaks": (i32, [P(f64), P(f64), vp]),
         "tusq_sample": (i32, [vp, i32, u64, u64, vp, vp]),
         "tusq_batch_create": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), i32, vp, P(vp)]),
         "tusq_batch_launch": (i32, [vp, vp]),
@@ -404,6 +405,13 @@ def tusq_dense_check(tc_mode: int, u, x_ptr: int, y_ptr: int, stream: int = 0) -
     _check(lib.tusq_dense_check(tc_mode, uu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream)),
            "tusq_dense_check")
+
+
+def tusq_measure_alu_peaks(stream: int = 0):
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.tusq_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(stream)))
+    return a.value, b.value
 
 
 def tusq_sample(probs_ptr: int, n_qubits: int, shots: int, seed: int, counts_ptr: int, stream: int = 0) -> None:

@@ -138,6 +138,21 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
         set_error("tusq_run_noalloc: max_window must be 0 (default) or in [4, 14]");
         return TUSQ_EINVAL;
     }
+    // the same range checks as tusq_run for the options this entry ignores:
+    // subtrees (one traversal), use_graph (direct launches), cache_states
+    // (no DFTT+Caching cache) and tc_mode (SIMT stages only)
+    if (o.subtrees < -1 || o.subtrees > 16) {
+        set_error("tusq_run_noalloc: subtrees must be in [-1, 16]");
+        return TUSQ_EINVAL;
+    }
+    if (o.cache_states < -1 || o.cache_states > 64) {
+        set_error("tusq_run_noalloc: cache_states must be in [-1, 64]");
+        return TUSQ_EINVAL;
+    }
+    if (o.tc_mode < TUSQ_TC_NONE || o.tc_mode > TUSQ_TC_TF32) {
+        set_error("tusq_run_noalloc: bad tc_mode");
+        return TUSQ_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const size_t amp = o.precision == TUSQ_C128 ? 16 : 8;
     const uint64_t dim = 1ULL << p->n;
@@ -173,6 +188,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
     Layout lay;
     std::vector<int> grid;
     int max_grid = 1;
+    bool sized = false;   // the snapshot count has been fitted to one compile's program size
     for (;;) {
         co.snapshots = k;
         try {
@@ -200,7 +216,18 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
                       "-byte static scratch; use tusq_run");
             return TUSQ_EINVAL;
         }
-        --k;
+        if (!sized) {
+            // the snapshots the scratch leaves room for beside this program
+            // (the program barely changes with the snapshot count), then at
+            // most a few more compiles stepping down
+            const size_t fixed = lay.total - state_bytes * (size_t)pg.n_snap_slots;
+            const size_t room = fixed < TUSQ_NOALLOC_SCRATCH_BYTES ? TUSQ_NOALLOC_SCRATCH_BYTES - fixed : 0;
+            k = std::min<int>(k - 1, (int)(room / state_bytes));
+            sized = true;
+        } else {
+            --k;
+        }
+        if (k < 0) k = 0;
     }
     auto at = [&](size_t off) { return (void *)(base + off); };
     double *records = (double *)at(lay.records), *partials = (double *)at(lay.partials);
@@ -208,8 +235,10 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
     int *restore_flag = (int *)at(lay.restore_flag);
     unsigned long long *counters = (unsigned long long *)at(lay.counters);
     void *state = at(lay.state), *snaps = at(lay.snaps);
-    // the program; the copies read pageable host memory, so they have
-    // completed when cudaMemcpyAsync returns
+    // the program: the copies read pageable host memory, which may be
+    // reused once cudaMemcpyAsync returns; the device writes are ordered on
+    // the stream, which is synchronised before this call returns (pg lives
+    // until then)
     if (!pg.ops.empty()) NA_TRY(cudaMemcpyAsync(at(lay.ops), pg.ops.data(), sizeof(DevOp) * pg.ops.size(), cudaMemcpyHostToDevice, st));
     if (!pg.mats.empty()) NA_TRY(cudaMemcpyAsync(at(lay.mats), pg.mats.data(), sizeof(double) * pg.mats.size(), cudaMemcpyHostToDevice, st));
     if (!pg.matsf.empty()) NA_TRY(cudaMemcpyAsync(at(lay.matsf), pg.matsf.data(), sizeof(float) * pg.matsf.size(), cudaMemcpyHostToDevice, st));

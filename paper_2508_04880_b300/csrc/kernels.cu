@@ -331,7 +331,7 @@ __device__ __forceinline__ SProg<R> load_program(const PassDesc &d, unsigned cha
 
 // The register stages of one pass on one tile in shared memory (tile bits
 // tb); threads beyond 2^(L-V) only take part in the barriers.
-template <typename R, int V>
+template <typename R, int V, bool DENSE = false>
 __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const PassDesc &d, const SProg<R> &P,
                                            int tid, uint64_t tb, DenseCtx *dc = nullptr) {
     using C2 = typename C2T<R>::type;
@@ -359,11 +359,11 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
             typename Phase<R>::U acc = 0;     // the stage's per-thread constant phase
             for (uint32_t k = 0; k < sd.op_count; ++k) {
                 const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
-                if (op.code == CODE_DENSE) {
+                if (DENSE && op.code == CODE_DENSE) {
                     // tensor cores: the stage's thread-independent run as one 32x32
                     // matrix (every thread of the CTA takes part); its fixed-bit
                     // terms join the per-thread constant phase
-                    if constexpr (sizeof(R) == 4 && V == 5) {
+                    if constexpr (DENSE && sizeof(R) == 4 && V == 5) {
                         if (op.csr[1] > op.csr[0] || op.phi0 != 0) {
                             if (!have_gfix) {
                                 gfix = tb;
@@ -420,7 +420,9 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
     }
 }
 
-template <typename R, int V>
+// DENSE: the instantiation for passes with tensor-core dense ops (complex64,
+// V = 5); the others carry none of that code.
+template <typename R, int V, bool DENSE = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
@@ -452,19 +454,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     __syncthreads();
 
     // tensor-core dense ops: 128 TMEM columns and a completion mbarrier
-    __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ int s_abort;
-    DenseCtx dctx{0u, 0u, 0u, args.err, &s_abort, args.dense_skip};
-    const bool dense = (flags & PF_DENSE) != 0;
-    // once a tensor-core wait of this traversal has run out, its later dense
-    // passes do nothing (the result is void and reported as a timeout)
-    if (dense && *args.err) return;
-    if (dense) {
+    DenseCtx dctx{0u, 0u, 0u, args.err, nullptr, args.dense_skip};
+    constexpr bool dense = DENSE;
+    if constexpr (DENSE) {
+        __shared__ uint32_t s_tmem;
+        __shared__ __align__(8) uint64_t s_mbar;
+        __shared__ int s_abort;
+        // once a tensor-core wait of this traversal has run out, its later
+        // dense passes do nothing (the result is void and reported as a timeout)
+        if (*args.err) return;
         if (tid == 0) s_abort = 0;
         dense_setup(&s_tmem, &s_mbar, tid);
         dctx.tmem = s_tmem;
         dctx.mbar = smem_u32(&s_mbar);
+        dctx.abort = &s_abort;
     }
 
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
@@ -496,8 +499,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
-        run_stages<R, V>(tile, d, P, tid, tb, dense ? &dctx : nullptr);
-        if (dense && s_abort) break;     // a tensor-core wait ran out: stop (uniform after the stage barrier)
+        run_stages<R, V, DENSE>(tile, d, P, tid, tb, dense ? &dctx : nullptr);
+        if constexpr (DENSE)
+            if (*dctx.abort) break;      // a tensor-core wait ran out: stop (uniform after the stage barrier)
         // store + epilogue
         float pn = 0.f, pr = 0.f, pi = 0.f;
         double dn = 0.0, dr = 0.0, di = 0.0;
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         }
         __syncthreads();
     }
-    if (dense) dense_teardown(dctx.tmem, tid);
+    if constexpr (DENSE) dense_teardown(dctx.tmem, tid);
     if (flags & PF_REDUCE) {
         // fixed-order block reduction: warp shuffles, then thread 0
         __shared__ double wsum[3][32];
@@ -637,33 +641,33 @@ __global__ void restore_kernel(C2 *state, const C2 *snap, uint64_t dim, const in
 
 // Allow the dynamic shared memory a pass tile needs (above the 48 KB
 // default); returns the attribute call's own status.
-template <typename R, int V>
+template <typename R, int V, bool DENSE = false>
 static cudaError_t allow_smem(size_t smem) {
     static size_t allowed = 48 * 1024;
     if (smem <= allowed) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, V, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) allowed = smem;
     return e;
 }
 
-template <typename R, int V>
+template <typename R, int V, bool DENSE = false>
 static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
     const size_t smem = ((sizeof(R) * 2) << a.d.L) + a.d.prog_bytes;
     const int threads = 1 << (a.d.L - V);
-    cudaError_t e = allow_smem<R, V>(smem);
+    cudaError_t e = allow_smem<R, V, DENSE>(smem);
     if (e != cudaSuccess) return e;
-    pass_kernel<R, V><<<grid, threads, smem, st>>>(a);
+    pass_kernel<R, V, DENSE><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R, int V>
+template <typename R, int V, bool DENSE = false>
 static int occupancy_t(int L, uint32_t prog_cap) {
     const size_t smem = ((sizeof(R) * 2) << L) + prog_cap;
     const int threads = 1 << (L - V);
     int nb = 0;
-    if (allow_smem<R, V>(smem) != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R, V>, threads, smem) != cudaSuccess)
+    if (allow_smem<R, V, DENSE>(smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R, V, DENSE>, threads, smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
@@ -682,7 +686,9 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaS
     case 2: return launch_pass_t<float, 2>(a, grid, st);
     case 3: return launch_pass_t<float, 3>(a, grid, st);
     case 4: return launch_pass_t<float, 4>(a, grid, st);
-    default: return launch_pass_t<float, 5>(a, grid, st);
+    default:
+        if (a.d.flags & PF_DENSE) return launch_pass_t<float, 5, true>(a, grid, st);
+        return launch_pass_t<float, 5>(a, grid, st);
     }
 }
 
@@ -703,7 +709,7 @@ int pass_occupancy(int precision, int V, int L, bool dense) {
     case 2: return occupancy_t<float, 2>(L, cap);
     case 3: return occupancy_t<float, 3>(L, cap);
     case 4: return occupancy_t<float, 4>(L, cap);
-    default: return occupancy_t<float, 5>(L, cap);
+    default: return dense ? occupancy_t<float, 5, true>(L, cap) : occupancy_t<float, 5>(L, cap);
     }
 }
 

@@ -110,6 +110,11 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi needs a moment to start: wait (at most 3 s) for its
+            # first sample so that short regions are sampled too
+            t_end = time.time() + 3.0
+            while not self.rows and time.time() < t_end:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -547,6 +552,44 @@ def served_subrun(args, T, torch):
             "plan_seconds": plan_s}
 
 
+def run_streamed_mode(args, T, torch):
+    """Config 2 without pruning: the 20-qubit depth-40 brickwork, every one of
+    the distinct instances of args.stream_shots shots kept (about 1e5 leaves),
+    traversed by tusq_run_streamed -- DFS chunks of args.chunk_leaves leaves
+    whose programs compile on host threads while the GPU runs the previous
+    chunks.  One step = one whole streamed traversal, compile included (the
+    program is never materialised whole).  Checked by the output's sum (the
+    tally weights sum to 1)."""
+    circ = W.WORKLOADS["brickwork_20q"]()
+    t0 = time.perf_counter()
+    pl = T.plan(circ, args.stream_shots, 0, prune=False)
+    plan_s = time.perf_counter() - t0
+    st = pl.stats()
+    probs = torch.empty(1 << circ.n_qubits, dtype=torch.float64, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    opts = T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT, tc_mode=args.tc_mode)
+    times, info = [], None
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = T.tusq_run_streamed(pl, probs.data_ptr(), args.chunk_leaves, opts, 0, sp)
+            times.append(time.perf_counter() - t0)
+    secs = min(times)
+    n_inst = st["n_instances"]
+    return {"metric": "noisy instances/s (streamed, unpruned)", "value": n_inst / secs, "unit": "instances/s",
+            "seconds_per_traversal": secs, "steps": len(times), "warmup": 0, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "20-qubit brickwork depth 40, Haar SU(2) + CZ, depolarizing 1e-3/1e-2, "
+                                   f"{args.stream_shots} shots, no pruning",
+                       "instances": n_inst, "chunk_leaves": args.chunk_leaves,
+                       "chunks": (n_inst + args.chunk_leaves - 1) // args.chunk_leaves,
+                       "compile_threads": "half the host cores", "tc_mode": args.tc_mode},
+            "plan_seconds": plan_s, "sum_probs": float(probs.sum()),
+            "run_info": {k: info[k] for k in ("passes", "gate_apps", "leaf_passes", "restores", "unrecovered",
+                                              "program_bytes", "algorithmic_bytes")},
+            "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,7 +610,9 @@ def main():
     ap.add_argument("--served-jobs", type=int, default=16)
     ap.add_argument("--served-max-qubits", type=int, default=26)
     ap.add_argument("--served-rate", type=float, default=0.75)
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity", "caching"],
+    ap.add_argument("--stream-shots", type=int, default=100_000)
+    ap.add_argument("--chunk-leaves", type=int, default=4096)
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "served", "fidelity", "caching", "streamed"],
                     help="main: the 28-qubit headline; batch: config 4; served: config 5; "
                          "fidelity: pruning delta and per-stage ablation")
     ap.add_argument("--fidelity-shots", type=int, default=20_000)
@@ -607,7 +652,7 @@ def main():
     torch.cuda.set_device(local)
     if args.mode != "main":
         line = {"batch": run_batch, "served": run_served, "fidelity": run_fidelity,
-                 "caching": run_caching}[args.mode](args, T, torch)
+                 "caching": run_caching, "streamed": run_streamed_mode}[args.mode](args, T, torch)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -386,6 +386,21 @@ int tusq_dense_check(int tc_mode, const double *u_host, const float *x_dev, floa
  * second.  The SM clock during the call is the caller's to sample. */
 int tusq_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops, void *cuda_stream);
 
+/* A traversal of a wide tree with bounded program memory: the DFS order is
+ * cut into ceil(N_l / chunk_leaves) chunks of nearly equal work (as
+ * tusq_plan_shard, the parallel-subtree cut of Sec. III-B), and the chunks
+ * traverse one after the other on cuda_stream, each from its own root state,
+ * all adding into probs_dev (caller-owned device buffer of 2^n doubles, zeroed
+ * first; the result is the same distribution as tusq_run's).  Each chunk's
+ * device program is compiled on one of `compile_threads` host threads (0 =
+ * half the cores) up to that many chunks ahead of the GPU, so compilation
+ * overlaps the traversal and only the programs of the chunks in flight
+ * exist.  Options as tusq_run (subtrees and use_graph are not used).
+ * Synchronises the stream; fills *info (optional) with the summed counters
+ * (program_bytes: the largest chunk's).  Errors as tusq_run. */
+int tusq_run_streamed(const tusq_plan_t *p, const tusq_run_opts *opts, uint64_t chunk_leaves,
+                      int compile_threads, double *probs_dev, void *cuda_stream, tusq_run_info_t *info);
+
 /* ------------------------------------------------------- shot sampling */
 
 /* Shots drawn from an output distribution on the device.  The paper samples

@@ -37,7 +37,7 @@ EXPORTS = [
     "tusq_exec_create",
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
-    "tusq_run", "tusq_run_noalloc", "tusq_dense_check", "tusq_measure_alu_peaks", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
+    "tusq_run", "tusq_run_noalloc", "tusq_run_streamed", "tusq_dense_check", "tusq_measure_alu_peaks", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_poll_device_interval", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
@@ -126,6 +126,7 @@ def _load():
         "tusq_exec_free": (None, [vp]),
         "tusq_run": (i32, [vp, P(RunOpts), vp, vp]),
         "tusq_run_noalloc": (i32, [vp, P(RunOpts), vp, vp, P(RunInfo)]),
+        "tusq_run_streamed": (i32, [vp, P(RunOpts), u64, i32, vp, vp, P(RunInfo)]),
         "tusq_dense_check": (i32, [i32, P(f64), vp, vp, vp]),
         "tusq_measure_alu_peaks": (i32, [P(f64), P(f64), vp]),
         "tusq_sample": (i32, [vp, i32, u64, u64, vp, vp]),
@@ -395,6 +396,18 @@ def tusq_run_noalloc(plan: Plan, probs_ptr: int, opts: Optional[RunOpts] = None,
     info = RunInfo()
     _check(lib.tusq_run_noalloc(plan.h, ctypes.byref(o), ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream),
                                 ctypes.byref(info)))
+    return info.as_dict()
+
+
+def tusq_run_streamed(plan: Plan, probs_ptr: int, chunk_leaves: int, opts: Optional[RunOpts] = None,
+                      compile_threads: int = 0, stream: int = 0) -> dict:
+    """The traversal as DFS chunks of about chunk_leaves leaves, compiled on
+    host threads ahead of the GPU; returns the summed run info."""
+    o = opts or run_opts()
+    info = RunInfo()
+    _check(lib.tusq_run_streamed(plan.h, ctypes.byref(o), chunk_leaves, compile_threads,
+                                 ctypes.c_void_p(probs_ptr), ctypes.c_void_p(stream), ctypes.byref(info)),
+           "tusq_run_streamed")
     return info.as_dict()
 
 

@@ -61,6 +61,7 @@ struct tusq_exec {
     // subtrees still to cut from `plan` (0: none)
     int pending_parts = 0;
     const tusq_plan_t *plan = nullptr;
+    bool accumulate = false;        // add into the output instead of overwriting it (streamed chunks)
     uint64_t launches = 0;
     size_t footprint = 0;
     bool profiling = false;
@@ -429,7 +430,7 @@ static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
         e->launches++;
         return TUSQ_OK;
     }
-    CUDA_TRY(cudaMemsetAsync(probs, 0, sizeof(double) * e->dim, st));
+    if (!e->accumulate) CUDA_TRY(cudaMemsetAsync(probs, 0, sizeof(double) * e->dim, st));
     CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(unsigned long long) * 4, st));
     if (pg.n_checks) {
         CUDA_TRY(cudaMemsetAsync(e->drift_log, 0, sizeof(double) * pg.n_checks, st));
@@ -612,6 +613,8 @@ int exec_launch(tusq_exec *e, double *probs, cudaStream_t st) {
     return TUSQ_OK;
 }
 
+void exec_set_accumulate(tusq_exec *e, bool on) { e->accumulate = on; }
+
 void exec_free(tusq_exec *e) {
     if (!e) return;
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
@@ -778,3 +781,11 @@ int tusq_run(const tusq_plan_t *p, const tusq_run_opts *opts, double *probs_dev,
 }
 
 }  // extern "C"
+
+namespace tusq {
+// Option validation and completion as tusq_exec_create does it (for the
+// other entry points built on the exec).
+int resolve_run_opts(const tusq_plan_t *p, const tusq_run_opts *opts, tusq_run_opts &o, const char *who) {
+    return resolve_opts(p, opts, o, who);
+}
+}  // namespace tusq

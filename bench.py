@@ -274,11 +274,12 @@ def run_reference(args, rank, world):
 
 
 def run_batch(args, T, torch):
-    """Config 4: many small noisy jobs of uneven depth.  Jobs that fit a CTA's
-    shared memory (<= 13 qubits, complex64) run in one persistent launch
-    replayed from a CUDA graph with autotuned options; larger ones run as
-    concurrent per-job traversals on several streams.  One step = every job
-    once."""
+    """Config 4: many noisy jobs of uneven size and depth in one persistent
+    launch replayed from a CUDA graph.  Jobs that fit a CTA's shared memory
+    (<= 13 qubits, complex64) run whole in one CTA; larger ones run on CTA
+    groups with their state in global memory, scheduled onto the grid by the
+    host.  Options (traversal, fusion schedule, CTAs per group) autotuned on
+    a sample of the jobs.  One step = every job once."""
     all_jobs = W.job_mix(args.jobs, seed=0, n_lo=12, n_hi=18, d_lo=20, d_hi=80)
     kept, all_plans, rejected, plan_s = plan_admitted(T, all_jobs, lambda j: args.batch_shots, args.max_job_work,
                                                       args.max_job_instances)
@@ -286,48 +287,44 @@ def run_batch(args, T, torch):
     plans = [all_plans[j] for j in kept]
     del all_plans
     n_inst = sum(p.stats()["n_instances"] for p in plans)
-    small = [i for i, c in enumerate(jobs) if c.n_qubits <= 13]
-    large = [i for i, c in enumerate(jobs) if c.n_qubits > 13]
     outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c in jobs]
     stream = torch.cuda.Stream()
-    side = [torch.cuda.Stream() for _ in range(args.streams)]
     base = T.run_opts(precision=T.C64)
+    sample = list(range(0, len(jobs), max(1, len(jobs) // 256)))[:256]
+    t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        best, tune_ms = T.tusq_batch_autotune([plans[i] for i in small], [outs[i].data_ptr() for i in small],
+        best, tune_ms = T.tusq_batch_autotune([plans[i] for i in sample], [outs[i].data_ptr() for i in sample],
                                               base, stream.cuda_stream)
-        b = T.Batch([plans[i] for i in small], [outs[i].data_ptr() for i in small], best, use_graph=True,
-                    stream=stream.cuda_stream)
-    # the per-job programs compile independently (the C calls release the GIL)
-    from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
-        exs = list(pool.map(lambda ki: T.Exec(plans[ki[1]], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT,
-                                                                       use_graph=int(args.graph),
-                                                                       tc_mode=args.tc_mode),
-                                              side[ki[0] % len(side)].cuda_stream), enumerate(large)))
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        b = T.Batch(plans, [o.data_ptr() for o in outs], best, use_graph=True, stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
 
     def step():
         b.launch(stream.cuda_stream)
-        for k, i in enumerate(large):
-            exs[k].launch(outs[i].data_ptr(), side[k % len(side)].cuda_stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    secs = (time.perf_counter() - t0) / args.steps
-    b.finish()
-    for e in exs:
-        e.finish()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    secs = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    info = b.finish()
     # error against the oracle (complex128, every instance from |0..0>) of the
-    # cheapest jobs of each group (instances x gates x 2^n), so that the check
+    # cheapest jobs of each kind (instances x gates x 2^n), so that the check
     # stays within seconds of host time
     import oracle
     errs = []
     cost = {i: plans[i].stats()["n_instances"] * jobs[i].n_gates * (1 << jobs[i].n_qubits) for i in range(len(jobs))}
-    for i in sorted(small, key=cost.get)[:2] + sorted(large, key=cost.get)[:1]:
+    small = [i for i, c in enumerate(jobs) if c.n_qubits <= 13]
+    group = [i for i, c in enumerate(jobs) if c.n_qubits > 13]
+    for i in sorted(small, key=cost.get)[:2] + sorted(group, key=cost.get)[:2]:
         ref, _ = oracle.run(jobs[i], args.batch_shots, kept[i])
         d = np.abs(outs[i].cpu().numpy() - ref)
         errs.append({"job": kept[i], "qubits": jobs[i].n_qubits, "max_abs": float(d.max()), "tv": float(d.sum())})
@@ -339,11 +336,15 @@ def run_batch(args, T, torch):
                                f"{args.batch_shots} shots each", "jobs_run": len(jobs),
                    "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
                    "max_job_instances": args.max_job_instances,
-                   "jobs_in_one_launch": len(small),
-                   "tc_mode_per_launch_jobs": ["none", "tf32x3", "bf16x3", "tf32"][args.tc_mode],
-                   "jobs_on_streams": len(large), "instances": n_inst,
-                   "autotuned": {"traversal": best.traversal, "schedule": best.schedule, "ms": tune_ms}},
-        "plan_seconds": plan_s, "error_vs_oracle": errs,
+                   "one_launch": {"single_cta_jobs": len(small), "group_jobs": b.group_jobs(),
+                                  "graph_replay": True},
+                   "instances": n_inst,
+                   "autotuned": {"traversal": best.traversal, "schedule": best.schedule,
+                                 "group_ctas": best.group_ctas or 16, "ms_on_sample": tune_ms,
+                                 "sample_jobs": len(sample), "seconds": tune_s}},
+        "plan_seconds": plan_s, "create_seconds": create_s, "error_vs_oracle": errs,
+        "run_info": {k: info[k] for k in ("passes", "gate_apps", "leaf_passes", "restores", "unrecovered")},
+        "clocks": clk.summary(),
     }
 
 

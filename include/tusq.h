@@ -262,6 +262,9 @@ typedef struct {
                                  matrix on the tensor cores instead of op by op (Sec. II, Eq. 1:
                                  a fused gate block applied to groups of 2^k amplitudes).
                                  TUSQ_TC_NONE (default) = never. Only 13-qubit pass tiles. */
+    int group_ctas;           /* batches only: most CTAs of the group running one job above one
+                                 CTA's shared memory (1..16; 0 = 16); a job never gets more CTAs
+                                 than its passes have tiles */
 } tusq_run_opts;
 
 /* Tensor-core precision of the dense stages (FP32 accumulation in TMEM):
@@ -426,12 +429,23 @@ int tusq_sample(const double *probs_dev, int n_qubits, uint64_t shots, uint64_t 
 
 typedef struct tusq_batch tusq_batch;   /* opaque */
 
-/* Many small jobs in one launch (the batching of Sec. III-B's traversal
- * across independent noisy simulations): each CTA of one persistent kernel
- * takes jobs from a work queue and runs a job's whole traversal with its
- * state held in shared memory -- jobs of 5..13 qubits (complex64) or 4..12
- * (complex128), of uneven depth and tree shape.  probs_dev[j] is job j's
- * caller-owned device output (2^n_j doubles, zeroed by the kernel).
+/* Many jobs in one launch (the batching of Sec. III-B's traversal across
+ * independent noisy simulations), of uneven size, depth and tree shape, in
+ * one persistent kernel:
+ *   - a job of 5..13 qubits (complex64; 4..12 complex128) runs whole in one
+ *     CTA with its state in shared memory, taken from a work queue;
+ *   - a larger one, up to 22 qubits (a "group job"), runs on a group of
+ *     k = min(2^(n-13), 16) CTAs (2^(n-12) for complex128) with its state in
+ *     global memory: each member takes its share of every pass's tiles, and
+ *     the group meets at a barrier after every step that writes the state.
+ *     The host assigns group jobs to CTAs before the launch (most work first,
+ *     onto the CTAs that fall free earliest, one order for all), and the
+ *     launch is cooperative so that every CTA is resident; a barrier's wait
+ *     is bounded (about 1 s), after which the batch stops and
+ *     tusq_batch_finish returns TUSQ_ETIMEOUT.
+ * A CTA first runs its group-job shares, then takes queued single-CTA jobs.
+ * probs_dev[j] is job j's caller-owned device output (2^n_j doubles, zeroed
+ * by the kernel).
  * use_graph != 0 records the launch into a CUDA graph on the first
  * tusq_batch_launch and replays it afterwards (needs a non-default stream).
  * Options as tusq_run (leaf peek is not used: the state never leaves the
@@ -439,13 +453,24 @@ typedef struct tusq_batch tusq_batch;   /* opaque */
 int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *opts,
                       double *const *probs_dev, int use_graph, void *cuda_stream, tusq_batch **out);
 int tusq_batch_launch(tusq_batch *b, void *cuda_stream);
-/* Synchronises; *info (optional) gets the summed counters of all jobs. */
+/* Synchronises; *info (optional) gets the summed counters of all jobs.
+ * TUSQ_ETIMEOUT if a group barrier's bounded wait ran out. */
 int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info);
+/* Number of group jobs (jobs above one CTA's shared memory) in the batch. */
+int tusq_batch_group_jobs(const tusq_batch *b);
+/* Test hook for the bounded group-barrier wait: when on, later launches make
+ * every group barrier wait for one member more than the group has, a
+ * dependency that never resolves; each wait runs out after about one second
+ * and tusq_batch_finish returns TUSQ_ETIMEOUT.  Nothing faults or hangs; the
+ * batch runs normally again once the hook is off. */
+int tusq_batch_set_stall_test(tusq_batch *b, int on);
 void tusq_batch_free(tusq_batch *b);
 
-/* Autotuner: times one batch launch for each traversal policy and fusion
- * schedule (starting from *base) and returns the fastest options in *best
- * (and its time in *best_ms). */
+/* Autotuner: times batch launches (one warm-up, one timed) while it tunes,
+ * one knob at a time from *base, the traversal policy (snapshot, uncompute,
+ * from scratch), the fusion schedule (window growth by lookahead or list
+ * order) and, when the batch has group jobs, the CTAs per group (16, 8, 4);
+ * returns the fastest options in *best (and its time in *best_ms). */
 int tusq_batch_autotune(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *base,
                         double *const *probs_dev, void *cuda_stream, tusq_run_opts *best,
                         double *best_ms);

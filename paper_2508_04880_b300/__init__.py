@@ -38,7 +38,7 @@ EXPORTS = [
     "tusq_exec_launch", "tusq_exec_finish", "tusq_compile_stats", "tusq_exec_set_record_bias",
     "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
     "tusq_run", "tusq_run_noalloc", "tusq_run_streamed", "tusq_dense_check", "tusq_measure_alu_peaks", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
-    "tusq_batch_free", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
+    "tusq_batch_free", "tusq_batch_group_jobs", "tusq_batch_set_stall_test", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
     "tusq_poll_device_interval", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
@@ -74,7 +74,7 @@ class RunOpts(ctypes.Structure):
                 ("leaf_peek", ctypes.c_int), ("root_reset", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("snapshot_bytes", ctypes.c_uint64), ("check_every", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("use_graph", ctypes.c_int), ("cache_states", ctypes.c_int),
-                ("subtrees", ctypes.c_int), ("tc_mode", ctypes.c_int)]
+                ("subtrees", ctypes.c_int), ("tc_mode", ctypes.c_int), ("group_ctas", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):
@@ -134,6 +134,8 @@ def _load():
         "tusq_batch_launch": (i32, [vp, vp]),
         "tusq_batch_finish": (i32, [vp, P(RunInfo)]),
         "tusq_batch_free": (None, [vp]),
+        "tusq_batch_group_jobs": (i32, [vp]),
+        "tusq_batch_set_stall_test": (i32, [vp, i32]),
         "tusq_batch_autotune": (i32, [P(vp), ctypes.c_uint32, P(RunOpts), P(vp), vp, P(RunOpts), P(f64)]),
         "tusq_server_create": (i32, [ctypes.c_size_t, i32, P(vp)]),
         "tusq_submit": (i32, [vp, vp, P(RunOpts), vp, P(u64)]),
@@ -466,9 +468,10 @@ def _ptr_array(ptrs):
 
 
 class Batch:
-    """Owns a tusq_batch: many small jobs (5..13 qubits complex64, 4..12
-    complex128) traversed by one persistent launch, optionally replayed from
-    a captured CUDA graph."""
+    """Owns a tusq_batch: many jobs (5..22 qubits complex64, 4..22 complex128)
+    traversed by one persistent launch -- single-CTA jobs with the state in
+    shared memory, larger ones on CTA groups -- optionally replayed from a
+    captured CUDA graph."""
 
     def __init__(self, plans, probs_ptrs, opts: Optional[RunOpts] = None, use_graph: bool = False,
                  stream: int = 0):
@@ -488,6 +491,12 @@ class Batch:
         info = RunInfo()
         _check(lib.tusq_batch_finish(self.h, ctypes.byref(info)))
         return info.as_dict()
+
+    def group_jobs(self) -> int:
+        return int(lib.tusq_batch_group_jobs(self.h))
+
+    def set_stall_test(self, on: bool) -> None:
+        _check(lib.tusq_batch_set_stall_test(self.h, int(bool(on))))
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -1,5 +1,8 @@
-// Batched execution of many small jobs in one launch (the job kernel), with
-// optional CUDA-graph replay and an autotuner over compile options.
+// Batched execution of many jobs in one persistent launch (the job kernel):
+// jobs whose state fits one CTA's shared memory run whole in one CTA; larger
+// ones (group jobs) run on groups of CTAs with their state in global memory,
+// scheduled on the host onto the CTAs.  Optional CUDA-graph replay and an
+// autotuner over compile options.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,7 +18,7 @@
 
 namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
-cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, cudaStream_t st);
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, bool cooperative, cudaStream_t st);
 int job_max_qubits_of(int precision);
 int job_occupancy(int precision);
 }  // namespace tusq
@@ -42,6 +45,16 @@ struct tusq_batch {
     double *d_records = nullptr;
     unsigned int *d_next = nullptr;
     unsigned long long *d_counters = nullptr;
+    // group jobs
+    int n_group = 0;
+    std::vector<uint32_t> small_ids;
+    unsigned char *d_gstate = nullptr;
+    double *d_gpart = nullptr;
+    unsigned int *d_bars = nullptr;      // one counter per group job, then abort and error words
+    GroupEntry *d_assign = nullptr;
+    uint32_t *d_assign_off = nullptr;
+    uint32_t *d_small = nullptr;
+    int stall_test = 0;
     cudaStream_t last_stream = nullptr;
     bool use_graph = false;
     cudaGraphExec_t graph = nullptr;
@@ -69,7 +82,8 @@ int upload(T **dst, const std::vector<T> &v, cudaStream_t st) {
 
 void free_batch_buffers(tusq_batch *b, cudaStream_t st) {
     void *bufs[] = {b->d_jobs, b->d_steps, b->d_passes, b->d_ops, b->d_mats, b->d_matsf, b->d_tmask,
-                    b->d_tphi, b->d_snaps, b->d_records, b->d_next, b->d_counters};
+                    b->d_tphi, b->d_snaps, b->d_records, b->d_next, b->d_counters, b->d_gstate, b->d_gpart,
+                    b->d_bars, b->d_assign, b->d_assign_off, b->d_small};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, st);
 }
@@ -89,9 +103,17 @@ int run_once(tusq_batch *b, cudaStream_t st) {
     a.next_job = b->d_next;
     a.counters = b->d_counters;
     a.drift_tol = b->drift_tol;
+    a.assign = b->d_assign;
+    a.assign_off = b->d_assign_off;
+    a.small_ids = b->d_small;
+    a.n_small = (int32_t)b->small_ids.size();
+    a.stall_test = b->stall_test;
+    a.abort = b->d_bars + b->n_group;
+    a.err = b->d_bars + b->n_group + 1;
     B_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int), st));
     B_TRY(cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned long long), st));
-    B_TRY(launch_jobs(a, b->precision, b->grid, st));
+    B_TRY(cudaMemsetAsync(b->d_bars, 0, sizeof(unsigned int) * (b->n_group + 2), st));
+    B_TRY(launch_jobs(a, b->precision, b->grid, b->n_group > 0, st));
     return TUSQ_OK;
 }
 
@@ -116,6 +138,10 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         set_error("tusq_batch_create: bad traversal");
         return TUSQ_EINVAL;
     }
+    if (o.group_ctas < 0 || o.group_ctas > kMaxGroupSize) {
+        set_error("tusq_batch_create: group_ctas must be in [0, 16]");
+        return TUSQ_EINVAL;
+    }
     const int vbits = o.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64;
     const int nmax = job_max_qubits_of(o.precision);
     for (uint32_t j = 0; j < n_jobs; ++j) {
@@ -123,9 +149,10 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
             set_error("tusq_batch_create: NULL plan or output");
             return TUSQ_EINVAL;
         }
-        if (plans[j]->n < vbits || plans[j]->n > nmax) {
+        if (plans[j]->n < vbits || plans[j]->n > kMaxGroupJobQubits) {
             set_error("tusq_batch_create: job " + std::to_string(j) + " has " + std::to_string(plans[j]->n) +
-                      " qubits; batched jobs need " + std::to_string(vbits) + ".." + std::to_string(nmax));
+                      " qubits; batched jobs need " + std::to_string(vbits) + ".." +
+                      std::to_string(kMaxGroupJobQubits));
             return TUSQ_EINVAL;
         }
     }
@@ -148,13 +175,21 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     std::vector<uint64_t> tmask, tphi;
     std::vector<size_t> snap_off, rec_off;
     size_t snap_bytes = 0, rec_count = 0;
+    // group jobs: their state, partial sums and barrier counter
+    std::vector<size_t> gstate_off, gpart_off;
+    std::vector<int> bar_of(n_jobs, -1);
+    std::vector<double> cost(n_jobs, 0.0);
+    size_t gstate_bytes = 0, gpart_count = 0;
+    const int tile_L = o.precision == TUSQ_C128 ? 12 : 13;
     auto opts_of = [&](const tusq_plan_t &P) {
         const size_t state = amp << P.n;
         CompileOpts co;
         co.precision = o.precision;
         co.max_window = 0;
         co.traversal = o.traversal;
-        co.leaf_peek = 0;              // the state lives in shared memory: leaf passes keep their result
+        // a single-CTA job's state lives in shared memory: its leaf passes keep
+        // their result; a group job's lives in global memory like tusq_run's
+        co.leaf_peek = P.n > nmax ? o.leaf_peek : 0;
         co.root_reset = o.root_reset;
         co.schedule = o.schedule;
         co.checks = o.drift_tol >= 0 && o.traversal != TUSQ_FROM_SCRATCH;
@@ -229,6 +264,19 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         rec_off.push_back(rec_count);
         rec_count += 4 * (size_t)std::max(pg.max_depth, 1);
         jd.acc = probs_dev[j];
+        if (P.n > nmax) {
+            const uint64_t ntiles = 1ull << (P.n - tile_L);
+            const int gmax = o.group_ctas > 0 ? std::min(o.group_ctas, kMaxGroupSize) : kMaxGroupSize;
+            jd.group_k = (int32_t)std::min<uint64_t>(ntiles, (uint64_t)gmax);
+            gstate_off.push_back(gstate_bytes);
+            gstate_bytes += state;
+            gpart_off.push_back(gpart_count);
+            gpart_count += 3 * (size_t)jd.group_k;
+            bar_of[j] = b->n_group++;
+            cost[j] = (double)pg.passes_count * (double)((ntiles + jd.group_k - 1) / jd.group_k) + pg.steps.size();
+        } else {
+            cost[j] = (double)pg.passes_count + pg.steps.size();
+        }
         b->jobs.push_back(jd);
         Program &t = b->totals;
         t.passes_count += pg.passes_count;
@@ -250,6 +298,9 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     }
     cudaError_t ce = cudaMallocAsync((void **)&b->d_snaps, std::max<size_t>(snap_bytes, 16), st);
     if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_records, sizeof(double) * std::max<size_t>(rec_count, 4), st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_gstate, std::max<size_t>(gstate_bytes, 16), st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_gpart, sizeof(double) * std::max<size_t>(gpart_count, 4), st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_bars, sizeof(unsigned int) * (b->n_group + 2), st);
     if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_next, 16, st);
     if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&b->d_counters, 4 * sizeof(unsigned long long), st);
     if (ce != cudaSuccess) {
@@ -261,6 +312,61 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     for (uint32_t j = 0; j < n_jobs; ++j) {
         b->jobs[j].snaps = b->d_snaps + snap_off[j];
         b->jobs[j].records = b->d_records + rec_off[j];
+        if (bar_of[j] >= 0) {
+            b->jobs[j].state = b->d_gstate + gstate_off[bar_of[j]];
+            b->jobs[j].partials = b->d_gpart + gpart_off[bar_of[j]];
+            b->jobs[j].bar = b->d_bars + bar_of[j];
+        }
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // with group jobs every CTA of the grid must be resident at once (a
+    // cooperative launch), and the grid is what the host schedules onto
+    const int resident = nsm * job_occupancy(o.precision);
+    b->grid = b->n_group ? resident : std::max(1, std::min<int>((int)n_jobs, resident));
+    // group jobs, most work first, each onto the k CTAs that fall free
+    // earliest (greedy list scheduling); every CTA's entries follow this one
+    // order, so no two groups wait for each other the other way round
+    std::vector<std::vector<GroupEntry>> lists(b->grid);
+    {
+        std::vector<uint32_t> order;
+        for (uint32_t j = 0; j < n_jobs; ++j)
+            if (bar_of[j] >= 0) order.push_back(j);
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+        std::vector<double> avail(b->grid, 0.0);
+        std::vector<int> idx(b->grid);
+        for (uint32_t j : order) {
+            const int k = b->jobs[j].group_k;
+            for (int c = 0; c < b->grid; ++c) idx[c] = c;
+            std::partial_sort(idx.begin(), idx.begin() + k, idx.end(), [&](int x, int y) {
+                return avail[x] < avail[y] || (avail[x] == avail[y] && x < y);
+            });
+            std::sort(idx.begin(), idx.begin() + k);
+            double start = 0;
+            for (int r = 0; r < k; ++r) start = std::max(start, avail[idx[r]]);
+            for (int r = 0; r < k; ++r) {
+                lists[idx[r]].push_back(GroupEntry{j, (uint32_t)r});
+                avail[idx[r]] = start + cost[j];
+            }
+        }
+        for (uint32_t j = 0; j < n_jobs; ++j)
+            if (bar_of[j] < 0) b->small_ids.push_back(j);
+        // single-CTA jobs from the queue, most work first
+        std::stable_sort(b->small_ids.begin(), b->small_ids.end(),
+                         [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+    }
+    std::vector<GroupEntry> assign;
+    std::vector<uint32_t> assign_off(1, 0);
+    for (const auto &l : lists) {
+        assign.insert(assign.end(), l.begin(), l.end());
+        assign_off.push_back((uint32_t)assign.size());
+    }
+    if ((rc = upload(&b->d_assign, assign, st)) || (rc = upload(&b->d_assign_off, assign_off, st)) ||
+        (rc = upload(&b->d_small, b->small_ids, st))) {
+        free_batch_buffers(b, st);
+        delete b;
+        return rc;
     }
     if ((rc = upload(&b->d_jobs, b->jobs, st))) {
         free_batch_buffers(b, st);
@@ -274,10 +380,6 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         set_error(std::string("tusq_batch_create: ") + cudaGetErrorString(ce));
         return TUSQ_ECUDA;
     }
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = std::max(1, std::min<int>((int)n_jobs, nsm * job_occupancy(o.precision)));
     b->last_stream = st;
     *out = b;
     return TUSQ_OK;
@@ -329,6 +431,8 @@ int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info) {
     B_TRY(cudaStreamSynchronize(b->last_stream));
     unsigned long long cnt[4] = {0, 0, 0, 0};
     B_TRY(cudaMemcpy(cnt, b->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    unsigned int err = 0;
+    B_TRY(cudaMemcpy(&err, b->d_bars + b->n_group + 1, sizeof err, cudaMemcpyDeviceToHost));
     if (info) {
         std::memset(info, 0, sizeof *info);
         const Program &t = b->totals;
@@ -345,12 +449,31 @@ int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info) {
         std::memcpy(&md, &cnt[2], sizeof md);
         info->max_drift = md;
     }
+    if (err) {
+        set_error("tusq_batch_finish: a group barrier's bounded wait ran out; the batch stopped early");
+        return TUSQ_ETIMEOUT;
+    }
     if (cnt[1]) {
         set_error("tusq_batch_finish: drift above tolerance at a branch node without a snapshot");
         return TUSQ_EDRIFT;
     }
     return TUSQ_OK;
 }
+
+int tusq_batch_set_stall_test(tusq_batch *b, int on) {
+    if (!b) {
+        set_error("tusq_batch_set_stall_test: NULL batch");
+        return TUSQ_EINVAL;
+    }
+    b->stall_test = on != 0;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return TUSQ_OK;
+}
+
+int tusq_batch_group_jobs(const tusq_batch *b) { return b ? b->n_group : 0; }
 
 void tusq_batch_free(tusq_batch *b) {
     if (!b) return;
@@ -370,41 +493,72 @@ int tusq_batch_autotune(const tusq_plan_t *const *plans, uint32_t n_jobs, const 
     tusq_run_opts_default(&o);
     if (base) o = *base;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int travs[3] = {TUSQ_DFTT_SNAPSHOT, TUSQ_DFTT, TUSQ_FROM_SCRATCH};
-    double best_t = 1e300;
-    bool found = false;
-    for (int tv : travs)
-        for (int sched = 0; sched < 2; ++sched) {
-            tusq_run_opts c = o;
-            c.traversal = tv;
-            c.schedule = sched;
-            tusq_batch *b = nullptr;
-            int rc = tusq_batch_create(plans, n_jobs, &c, probs_dev, 0, cuda_stream, &b);
-            if (rc) return rc;
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            rc = tusq_batch_launch(b, cuda_stream);          // warm-up
-            float ms = 0;
-            if (!rc) {
-                cudaEventRecord(e0, st);
-                rc = tusq_batch_launch(b, cuda_stream);
-                cudaEventRecord(e1, st);
-            }
-            if (!rc) rc = tusq_batch_finish(b, nullptr);
-            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            tusq_batch_free(b);
-            if (rc) return rc;
-            if (ms < best_t) {
-                best_t = ms;
-                *best = c;
-                found = true;
-            }
+    bool has_group = false;
+    for (uint32_t j = 0; j < n_jobs; ++j)
+        if (plans[j] && plans[j]->n > job_max_qubits_of(o.precision)) has_group = true;
+    // time one configuration: a warm-up launch, then one timed launch
+    auto measure = [&](const tusq_run_opts &c, double *ms_out) -> int {
+        tusq_batch *b = nullptr;
+        int rc = tusq_batch_create(plans, n_jobs, &c, probs_dev, 0, cuda_stream, &b);
+        if (rc) return rc;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        rc = tusq_batch_launch(b, cuda_stream);
+        float ms = 0;
+        if (!rc) {
+            cudaEventRecord(e0, st);
+            rc = tusq_batch_launch(b, cuda_stream);
+            cudaEventRecord(e1, st);
         }
+        if (!rc) rc = tusq_batch_finish(b, nullptr);
+        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tusq_batch_free(b);
+        *ms_out = ms;
+        return rc;
+    };
+    // coordinate descent: traversal, then schedule, then CTAs per group job
+    tusq_run_opts cur = o;
+    double best_t = 1e300;
+    {
+        const int travs[3] = {TUSQ_DFTT_SNAPSHOT, TUSQ_DFTT, TUSQ_FROM_SCRATCH};
+        tusq_run_opts pick = cur;
+        for (int tv : travs) {
+            tusq_run_opts c = cur;
+            c.traversal = tv;
+            double ms;
+            const int rc = measure(c, &ms);
+            if (rc) return rc;
+            if (ms < best_t) { best_t = ms; pick = c; }
+        }
+        cur = pick;
+    }
+    {
+        tusq_run_opts c = cur;
+        c.schedule = 1 - cur.schedule;
+        double ms;
+        const int rc = measure(c, &ms);
+        if (rc) return rc;
+        if (ms < best_t) { best_t = ms; cur = c; }
+    }
+    if (has_group) {
+        const int sizes[2] = {8, 4};
+        tusq_run_opts pick = cur;
+        for (int g : sizes) {
+            tusq_run_opts c = cur;
+            c.group_ctas = g;
+            double ms;
+            const int rc = measure(c, &ms);
+            if (rc) return rc;
+            if (ms < best_t) { best_t = ms; pick = c; }
+        }
+        cur = pick;
+    }
+    *best = cur;
     if (best_ms) *best_ms = best_t;
-    return found ? TUSQ_OK : TUSQ_EINVAL;
+    return TUSQ_OK;
 }
 
 }  // extern "C"

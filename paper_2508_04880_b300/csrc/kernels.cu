@@ -420,29 +420,29 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
     }
 }
 
-// DENSE: the instantiation for passes with tensor-core dense ops (complex64,
-// V = 5); the others carry none of that code.
-template <typename R, int V, bool DENSE = false>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
+// The tiles first, first + stride, ... of one pass for this CTA: load (from
+// src), register stages, store and epilogue (state, snapshot, FP64 leaf
+// accumulation, partial sums of the norm and checksum into partial_out[0..2]
+// when the pass reduces).  The pass's program is in shared memory (P); the
+// first statement of the tile loop waits for it.
+template <typename R, int V, bool DENSE>
+__device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, void *statev, void *snapv, double *acc,
+                                          double *partial_out, const SProg<R> &P, unsigned char *smem_raw,
+                                          uint64_t first, uint64_t stride, DenseCtx &dctx) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
     // complex64 threads move adjacent pairs in the load/store phases
     constexpr int NROW = kC128 ? NR : NR / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PassDesc &d = args.d;
     const int L = d.L;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     C2 *tile = reinterpret_cast<C2 *>(smem_raw);
-    C2 *state = reinterpret_cast<C2 *>(args.state);
-    const C2 *srcp = reinterpret_cast<const C2 *>(args.src);   // tile loads (state or a snapshot)
-    C2 *snap = reinterpret_cast<C2 *>(args.snap);
+    C2 *state = reinterpret_cast<C2 *>(statev);
+    const C2 *srcp = reinterpret_cast<const C2 *>(srcv);   // tile loads (state or a snapshot)
+    C2 *snap = reinterpret_cast<C2 *>(snapv);
     const uint32_t flags = d.flags;
-
-    // the pass's program into shared memory (ops, matrices, diagonal terms)
-    const SProg<R> P = load_program<R>(d, smem_raw + (sizeof(C2) << L), args.ops, args.mats, args.matsf,
-                                       args.tmask, args.tphi, tid, nthr);
+    (void)nthr;
 
     // this thread's part of a load row (local index tid, or 2 tid for pairs)
     const uint32_t erow = kC128 ? (uint32_t)tid : (uint32_t)tid << 1;
@@ -453,22 +453,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     const float wleaf = (float)d.leaf_w;
     __syncthreads();
 
-    // tensor-core dense ops: 128 TMEM columns and a completion mbarrier
-    DenseCtx dctx{0u, 0u, 0u, args.err, nullptr, args.dense_skip};
-    constexpr bool dense = DENSE;
-    if constexpr (DENSE) {
-        __shared__ uint32_t s_tmem;
-        __shared__ __align__(8) uint64_t s_mbar;
-        __shared__ int s_abort;
-        // once a tensor-core wait of this traversal has run out, its later
-        // dense passes do nothing (the result is void and reported as a timeout)
-        if (*args.err) return;
-        if (tid == 0) s_abort = 0;
-        dense_setup(&s_tmem, &s_mbar, tid);
-        dctx.tmem = s_tmem;
-        dctx.mbar = smem_u32(&s_mbar);
-        dctx.abort = &s_abort;
-    }
 
     double red_n = 0.0, red_r = 0.0, red_i = 0.0;
 
@@ -477,10 +461,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     // (carries skip the positions outside the mask)
     uint64_t tb = 0, tstride = 0;
     for (int b = 0; b < d.n_cw; ++b) {
-        if (blockIdx.x >> b & 1) tb |= 1ull << d.cw[b];
-        if (gridDim.x >> b & 1) tstride |= 1ull << d.cw[b];
+        if (first >> b & 1) tb |= 1ull << d.cw[b];
+        if (stride >> b & 1) tstride |= 1ull << d.cw[b];
     }
-    for (uint64_t t = blockIdx.x; t < d.ntiles; t += gridDim.x, tb = ((tb | ~d.cwmask) + tstride) & d.cwmask) {
+    for (uint64_t t = first; t < d.ntiles; t += stride, tb = ((tb | ~d.cwmask) + tstride) & d.cwmask) {
         const uint64_t gbase = tb | gthr;
         // load the tile: every row load in flight before the shared stores
         if constexpr (kC128) {
@@ -499,7 +483,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
-        run_stages<R, V, DENSE>(tile, d, P, tid, tb, dense ? &dctx : nullptr);
+        run_stages<R, V, DENSE>(tile, d, P, tid, tb, DENSE ? &dctx : nullptr);
         if constexpr (DENSE)
             if (*dctx.abort) break;      // a tensor-core wait ran out: stop (uniform after the stage barrier)
         // store + epilogue
@@ -512,7 +496,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
                 C2 v = tile[sthr ^ d.srow[i]];
                 if (flags & PF_WRITE) state[g] = v;
                 if (flags & PF_SNAPSHOT) snap[g] = v;
-                if (flags & PF_LEAF) args.acc[g] = fma(d.leaf_w, v.x * v.x + v.y * v.y, args.acc[g]);
+                if (flags & PF_LEAF) acc[g] = fma(d.leaf_w, v.x * v.x + v.y * v.y, acc[g]);
                 if (flags & PF_REDUCE) {
                     const double h = check_sign(g);
                     dn += v.x * v.x + v.y * v.y;
@@ -524,7 +508,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
             const float4 *ts = reinterpret_cast<const float4 *>(tile);
             if (flags & PF_LEAF) {
                 // every accumulator load in flight before the updates
-                double2 *accp = reinterpret_cast<double2 *>(args.acc);
+                double2 *accp = reinterpret_cast<double2 *>(acc);
                 double2 ab[NROW];
 #pragma unroll
                 for (int i = 0; i < NROW; ++i) ab[i] = accp[(gbase | d.grow[i]) >> 1];
@@ -575,11 +559,42 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         if (tid == 0) {
             double a0 = 0, a1 = 0, a2 = 0;
             for (int w = 0; w < nw; ++w) { a0 += wsum[0][w]; a1 += wsum[1][w]; a2 += wsum[2][w]; }
-            args.partials[3 * blockIdx.x + 0] = a0;
-            args.partials[3 * blockIdx.x + 1] = a1;
-            args.partials[3 * blockIdx.x + 2] = a2;
+            partial_out[0] = a0;
+            partial_out[1] = a1;
+            partial_out[2] = a2;
         }
     }
+}
+
+// DENSE: the instantiation for passes with tensor-core dense ops (complex64,
+// V = 5); the others carry none of that code.
+template <typename R, int V, bool DENSE = false>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
+    using C2 = typename C2T<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PassDesc &d = args.d;
+    const int tid = threadIdx.x;
+    // the pass's program into shared memory (ops, matrices, diagonal terms)
+    const SProg<R> P = load_program<R>(d, smem_raw + (sizeof(C2) << d.L), args.ops, args.mats, args.matsf,
+                                       args.tmask, args.tphi, tid, blockDim.x);
+    // tensor-core dense ops: 128 TMEM columns and a completion mbarrier
+    DenseCtx dctx{0u, 0u, 0u, args.err, nullptr, args.dense_skip};
+    if constexpr (DENSE) {
+        __shared__ uint32_t s_tmem;
+        __shared__ __align__(8) uint64_t s_mbar;
+        __shared__ int s_abort;
+        // once a tensor-core wait of this traversal has run out, its later
+        // dense passes do nothing (the result is void and reported as a timeout)
+        if (*args.err) return;
+        if (tid == 0) s_abort = 0;
+        dense_setup(&s_tmem, &s_mbar, tid);
+        dctx.tmem = s_tmem;
+        dctx.mbar = smem_u32(&s_mbar);
+        dctx.abort = &s_abort;
+    }
+
+    pass_body<R, V, DENSE>(d, args.src, args.state, args.snap, args.acc, args.partials + 3 * blockIdx.x, P,
+                           smem_raw, blockIdx.x, gridDim.x, dctx);
 }
 
 // state <- |0..0>
@@ -749,11 +764,127 @@ cudaError_t launch_restore(void *state, const void *snap, int precision, uint64_
 // complex128 amplitudes (64 KiB).
 template <typename R> constexpr int job_max_qubits() { return sizeof(R) == 4 ? 13 : 12; }
 
-// job_kernel: each CTA takes jobs from a work queue and runs a job's whole
-// program -- resets, fused passes (register stages on the state held in
-// shared memory), leaf accumulation into the job's FP64 output, snapshot
-// writes and restores, drift records and checks -- without leaving the
-// CTA.  Jobs of uneven size and depth share one launch.
+// Barrier of the k CTAs running one group job: every member adds one to the
+// job's counter and waits until it reaches `target` (k times the barriers
+// passed so far).  The wait is bounded (about 1 s of SM clock, or until
+// another group gave up): it then sets the batch's error word and abort
+// flag and returns false.
+__device__ __forceinline__ bool group_barrier(const BatchArgs &B, unsigned int *bar, unsigned int target,
+                                              int tid) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const long long t0 = clock64();
+        int ok = 1;
+        for (;;) {
+            unsigned int v, ab;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(B.abort) : "memory");
+            if (ab) { ok = 0; break; }
+            if (clock64() - t0 > (2ll << 30)) {
+                atomicOr(B.err, 1u);
+                atomicExch(B.abort, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(128);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Member `rank` of the k-CTA group running job j: its share of every step --
+// amplitudes rank*T + tid (+ k*T ...) of resets and restores, tiles rank,
+// rank + k, ... of every pass (state and snapshots in global memory) -- with
+// a group barrier after each step that writes the state.  Records and drift
+// checks read the members' partial sums after the pass barrier; every member
+// takes the same restore decision, only rank 0 writes records and counters.
+// Returns false when a barrier gave up.
+template <typename R, int V>
+__device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char *smem_raw, unsigned char *pbase) {
+    using C2 = typename C2T<R>::type;
+    __shared__ int s_restore;
+    const JobDesc &J = B.jobs[j];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int k = J.group_k;
+    const uint64_t dim = 1ull << J.n;
+    const uint64_t first = (uint64_t)rank * nthr + tid, step = (uint64_t)k * nthr;
+    C2 *state = reinterpret_cast<C2 *>(J.state);
+    const C2 *snaps = reinterpret_cast<const C2 *>(J.snaps);
+    unsigned int nb = 0;
+    const unsigned int width = (unsigned int)(k + (B.stall_test ? 1 : 0));
+    for (uint64_t e = first; e < dim; e += step) J.acc[e] = 0.0;
+    for (uint32_t s = 0; s < J.nsteps; ++s) {
+        const Step &st = B.steps[J.step0 + s];
+        if (st.type == ST_INIT) {
+            for (uint64_t e = first; e < dim; e += step) {
+                C2 z;
+                z.x = (e == 0) ? 1 : 0;
+                z.y = 0;
+                state[e] = z;
+            }
+            if (!group_barrier(B, J.bar, width * ++nb, tid)) return false;
+        } else if (st.type == ST_PASS) {
+            const PassDesc &d = B.passes[st.pass];
+            const SProg<R> P = load_program<R>(d, pbase, B.ops, B.mats, B.matsf, B.tmask, B.tphi, tid, nthr);
+            const void *src = d.src_snap >= 0 ? (const void *)(snaps + dim * d.src_snap) : (const void *)state;
+            void *snap = (d.flags & PF_SNAPSHOT) ? (void *)(snaps + dim * d.snap) : nullptr;
+            DenseCtx none{0u, 0u, 0u, nullptr, nullptr, 0};
+            pass_body<R, V, false>(d, src, state, snap, J.acc, J.partials + 3 * rank, P, smem_raw, (uint64_t)rank,
+                                   (uint64_t)k, none);
+            if (!group_barrier(B, J.bar, width * ++nb, tid)) return false;
+        } else if (st.type == ST_RECORD || st.type == ST_CHECK) {
+            if (tid == 0) {
+                double n2 = 0, cr = 0, ci = 0;
+                for (int m = 0; m < k; ++m) {
+                    n2 += J.partials[3 * m];
+                    cr += J.partials[3 * m + 1];
+                    ci += J.partials[3 * m + 2];
+                }
+                double *rec = J.records + 4 * st.depth;
+                if (st.type == ST_RECORD) {
+                    if (rank == 0) {
+                        rec[0] = n2;
+                        rec[1] = cr;
+                        rec[2] = ci;
+                    }
+                } else {
+                    const double dn = fabs(sqrt(n2) - sqrt(fmax(rec[0], 0.0)));
+                    const double dc = hypot(cr - rec[1], ci - rec[2]);
+                    const double drift = fmax(dn, dc);
+                    const bool bad = drift > B.drift_tol;
+                    s_restore = bad && st.snap >= 0;
+                    if (rank == 0) {
+                        if (bad) atomicAdd(B.counters + (st.snap >= 0 ? 0 : 1), 1ull);
+                        atomicMax(B.counters + 2, (unsigned long long)__double_as_longlong(drift));
+                    }
+                }
+            }
+            __syncthreads();
+        } else if (st.type == ST_RESTORE) {
+            if (st.check < 0 || s_restore) {
+                const C2 *sn = snaps + dim * st.snap;
+                for (uint64_t e = first; e < dim; e += step) state[e] = sn[e];
+            }
+            if (!group_barrier(B, J.bar, width * ++nb, tid)) return false;
+        }
+    }
+    return true;
+}
+
+// job_kernel: the persistent launch of a batch.  First each CTA runs its
+// share of the group jobs (more amplitudes than one CTA's shared memory
+// holds) in the order the host assigned; then it takes single-CTA jobs from
+// a work queue and runs each job's whole program -- resets, fused passes
+// (register stages on the state held in shared memory), leaf accumulation
+// into the job's FP64 output, snapshot writes and restores, drift records
+// and checks -- without leaving the CTA.  Jobs of uneven size and depth
+// share one launch.
 template <typename R, int V>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const __grid_constant__ BatchArgs B) {
     using C2 = typename C2T<R>::type;
@@ -766,12 +897,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
     __shared__ double s_red[3];
     __shared__ double s_wsum[3][8];
     const int tid = threadIdx.x, nthr = blockDim.x;
+    for (uint32_t a = B.assign_off[blockIdx.x]; a < B.assign_off[blockIdx.x + 1]; ++a)
+        if (!run_group_job<R, V>(B, (int)B.assign[a].job, (int)B.assign[a].rank, smem_raw, pbase)) return;
     for (;;) {
         if (tid == 0) s_job = (int)atomicAdd(B.next_job, 1u);
         __syncthreads();
-        const int j = s_job;
+        const int q = s_job;
         __syncthreads();
-        if (j >= B.n_jobs) break;
+        if (q >= B.n_small) break;
+        const int j = (int)B.small_ids[q];
         const JobDesc &J = B.jobs[j];
         const int N = 1 << J.n;
         for (int e = tid; e < N; e += nthr) J.acc[e] = 0.0;
@@ -864,18 +998,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
 }
 
 template <typename R, int V>
-static cudaError_t launch_job_t(const BatchArgs &b, int grid, cudaStream_t st) {
+static cudaError_t launch_job_t(const BatchArgs &b, int grid, bool cooperative, cudaStream_t st) {
     const size_t smem = (sizeof(R) * 2 << job_max_qubits<R>()) + kMaxPassProgramBytes;
     cudaError_t e = cudaFuncSetAttribute(job_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    job_kernel<R, V><<<grid, 256, smem, st>>>(b);
+    // group jobs wait at barriers for CTAs of the same launch: the
+    // cooperative attribute guarantees that the whole grid is resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = cooperative ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, job_kernel<R, V>, b);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 // One launch over every job of a batch; `grid` CTAs drain the work queue.
-cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, cudaStream_t st) {
-    if (precision == TUSQ_C128) return launch_job_t<double, kRegBitsC128>(b, grid, st);
-    return launch_job_t<float, kRegBitsC64>(b, grid, st);
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, bool cooperative, cudaStream_t st) {
+    if (precision == TUSQ_C128) return launch_job_t<double, kRegBitsC128>(b, grid, cooperative, st);
+    return launch_job_t<float, kRegBitsC64>(b, grid, cooperative, st);
 }
 
 int job_max_qubits_of(int precision) {

@@ -219,11 +219,27 @@ struct PassArgs {
 struct JobDesc {
     uint32_t step0, nsteps;
     int32_t n;
-    int32_t pad;
+    int32_t group_k;       // 0: the job runs in one CTA with its state in shared
+                           // memory; k > 0: a group of k CTAs runs it with the
+                           // state in global memory, meeting at a barrier after
+                           // every pass
     double *acc;           // 2^n FP64 output (zeroed by the kernel)
     void *snaps;           // snapshot slots, 2^n amplitudes each
     double *records;       // 4 doubles per record depth
+    void *state;           // group jobs: the state (2^n amplitudes)
+    double *partials;      // group jobs: 3 doubles per group member (norm, checksum)
+    unsigned int *bar;     // group jobs: barrier counter (zeroed before each launch)
 };
+
+// One entry of a CTA's group-job list: the job and the CTA's rank in its group.
+struct GroupEntry {
+    uint32_t job, rank;
+};
+
+// Batched jobs above one CTA's shared memory run on groups of at most
+// kMaxGroupSize CTAs; the largest state a batch takes (32 MiB complex64).
+constexpr int kMaxGroupSize = 16;
+constexpr int kMaxGroupJobQubits = 22;
 
 struct BatchArgs {
     const JobDesc *jobs;
@@ -239,6 +255,17 @@ struct BatchArgs {
     unsigned int *next_job;          // work queue head (zeroed before each launch)
     unsigned long long *counters;    // [0] restores after failed checks, [1] unrecovered drift
     double drift_tol;
+    // group jobs: CTA b runs the (job, rank) entries assign[assign_off[b] ..
+    // assign_off[b + 1]) in that order -- one global order of the group jobs,
+    // so no two CTAs wait for each other the other way round -- then takes
+    // single-CTA jobs small_ids[next_job++] until none is left
+    const GroupEntry *assign;
+    const uint32_t *assign_off;
+    const uint32_t *small_ids;
+    int32_t n_small;
+    int32_t stall_test;              // test hook: group barriers wait for one member too many
+    unsigned int *abort;             // set when a group barrier's bounded wait ran out
+    unsigned int *err;               // bit 0: a bounded wait ran out
 };
 
 // Fuse every unconditional snapshot restore into the pass that follows it

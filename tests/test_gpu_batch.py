@@ -94,7 +94,77 @@ def test_batch_autotune_and_size_limits():
     outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
     best, ms = T.tusq_batch_autotune(plans, [o.data_ptr() for o in outs], T.run_opts(precision=T.C64))
     assert ms > 0 and best.traversal in (T.DFTT, T.FROM_SCRATCH, T.DFTT_SNAPSHOT) and best.schedule in (0, 1)
-    big = T.plan(W.brickwork(14, 2, 0, 0.0, 0.0), 10, 0)
-    o = torch.empty(1 << 14, dtype=torch.float64, device="cuda")
+    assert best.group_ctas in (0, 4, 8, 16)
+    # group jobs go up to 22 qubits; a 23-qubit job is refused before any allocation
+    big = T.plan(W.brickwork(23, 1, 0, 0.0, 0.0), 10, 0)
     with pytest.raises(T.TusqError):
-        T.Batch([big], [o.data_ptr()], T.run_opts(precision=T.C64))
+        T.Batch([big], [0x1000], T.run_opts(precision=T.C64))
+
+
+def _mixed_jobs():
+    # single-CTA jobs and group jobs (14-18 qubits: 2-32 tiles of 2^13
+    # amplitudes, groups of 2-16 CTAs, state in global memory) in one launch
+    return [
+        (W.brickwork(14, 8, 11, 2e-3, 2e-2), 5_000, 11),
+        (W.qaoa_3regular(16, 2, 12, 1e-3, 1e-2), 5_000, 12),
+        (W.random_layers(6, 20, 13, 1e-3, 1e-2), 5_000, 13),
+        (W.brickwork(18, 6, 14, 2e-3, 2e-2), 3_000, 14),
+        (W.brickwork(12, 10, 15, 1e-3, 1e-2), 10_000, 15),
+        (W.qaoa_3regular(14, 3, 16, 1e-3, 1e-2), 10_000, 16),
+    ]
+
+
+@pytest.fixture(scope="module")
+def mixed_refs():
+    jobs = _mixed_jobs()
+    return jobs, [oracle.run(c, s, seed)[0] for c, s, seed in jobs]
+
+
+@pytest.mark.parametrize("precision", [T.C64, T.C128])
+@pytest.mark.parametrize("traversal", [T.DFTT, T.DFTT_SNAPSHOT])
+def test_group_jobs_match_oracle(mixed_refs, precision, traversal):
+    import torch
+    jobs, refs = mixed_refs
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    b = T.Batch(plans, [o.data_ptr() for o in outs], T.run_opts(precision=precision, traversal=traversal))
+    assert b.group_jobs() == sum(1 for c, _, _ in jobs if c.n_qubits > (12 if precision == T.C128 else 13))
+    b.launch()
+    info = b.finish()
+    assert info["unrecovered"] == 0
+    for (c, s, seed), o, ref in zip(jobs, outs, refs):
+        _close(o.cpu().numpy(), ref, precision, c.name)
+
+
+def test_group_jobs_graph_replay_and_bounded_barrier():
+    # replayed from a CUDA graph: the same result every time; then the test
+    # hook makes every group barrier wait for one member too many -- a
+    # dependency that never resolves -- so the bounded waits run out and the
+    # batch reports TUSQ_ETIMEOUT; with the hook off it runs normally again
+    import torch
+    jobs = _mixed_jobs()
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = T.Batch(plans, [o.data_ptr() for o in outs], T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT),
+                    use_graph=True, stream=stream.cuda_stream)
+        first = None
+        for _ in range(3):
+            b.launch(stream.cuda_stream)
+            b.finish()
+            now = [o.cpu().numpy() for o in outs]
+            if first is None:
+                first = now
+            for a_, c_ in zip(first, now):
+                assert np.array_equal(a_, c_)
+        b.set_stall_test(True)
+        b.launch(stream.cuda_stream)
+        with pytest.raises(T.TusqError) as e:
+            b.finish()
+        assert e.value.code == T.TUSQ_ETIMEOUT
+        b.set_stall_test(False)
+        b.launch(stream.cuda_stream)
+        b.finish()
+        for a_, o in zip(first, outs):
+            assert np.array_equal(a_, o.cpu().numpy())

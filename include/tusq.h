@@ -304,6 +304,7 @@ typedef struct {
     uint64_t rederives;           /* returns re-derived forward from a snapshot above or |0..0>
                                      (no usable state below a non-invertible layer) */
     uint64_t dense_ops;           /* tensor-core dense ops (tc_mode): 32x32 matrices */
+    uint64_t chunks;              /* parallel-subtree chunks the traversal ran as (1: one) */
 } tusq_run_info_t;
 
 /* Compile a plan into a device program for the current device and allocate

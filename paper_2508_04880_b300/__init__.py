@@ -84,7 +84,7 @@ class RunInfo(ctypes.Structure):
         [(f, ctypes.c_double) for f in ("max_drift", "state_bytes", "algorithmic_bytes",
                                         "program_bytes")] + \
         [(f, ctypes.c_uint64) for f in ("stages", "matrix_ops", "diag_ops", "diag_terms", "cache_restores",
-                                        "rederives", "dense_ops")]
+                                        "rederives", "dense_ops", "chunks")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -542,6 +542,7 @@ int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
             e->prof_bytes.insert(e->prof_bytes.end(), q->prof_bytes.begin(), q->prof_bytes.end());
         }
         sum.kernel_launches = e->launches;
+        sum.chunks = e->parts.size();
         if (info) *info = sum;
         return rc_all;
     }
@@ -563,6 +564,7 @@ int exec_finish(tusq_exec *e, tusq_run_info_t *info) {
         info->unrecovered = cnt[1];
         info->kernel_launches = e->launches;
         info->max_drift = maxd;
+        info->chunks = 1;
     }
     if (cnt[3]) {
         set_error("a bounded device wait for the tensor cores ran out; the traversal stopped early");

@@ -136,3 +136,24 @@ def test_automatic_chunk_count(n):
     for precision in (T.C128, T.C64):
         got, info = _gpu(pl, precision=precision, traversal=T.DFTT_SNAPSHOT, subtrees=-1)
         close(got, ref, precision, f"n {n}")
+        # the rule: chunks until the passes in flight offer about twice the
+        # CTA slots, at most 16 -- a 6-qubit pass is one tile (16 chunks), a
+        # 23-qubit complex64 pass already has 1024 tiles (one chunk)
+        if n == 6:
+            assert info["chunks"] == 16, info["chunks"]
+        if n == 18:
+            # 32 complex64 tiles of 2^13 (2 CTAs per SM) or 64 complex128 tiles
+            # of 2^12 (1 CTA per SM) against 148 SMs
+            assert info["chunks"] == (16 if precision == T.C64 else 5), (precision, info["chunks"])
+
+
+@pytest.mark.gpu
+def test_automatic_chunk_count_one_chunk_at_23_qubits():
+    # a 23-qubit complex64 pass has 1024 tiles, more than twice the CTA
+    # slots: the automatic rule keeps one traversal
+    import torch
+    c = W.brickwork(23, 2, 3, 0.0, 0.0)
+    pl = T.tusq_plan_from_instances(T.circuit_from(c), [[], [(0, 0, 1)]], np.array([0.5, 0.5]))
+    got, info = _gpu(pl, precision=T.C64, traversal=T.DFTT_SNAPSHOT, subtrees=-1)
+    assert info["chunks"] == 1
+    assert abs(float(np.sum(got)) - 1.0) < 1e-5

@@ -426,9 +426,7 @@ struct Encoder {
     uint32_t op_bytes(const HOp &o) const {
         const uint32_t mb = c128 ? 256u : 128u;
         if (o.type == H_DIAG) return (uint32_t)sizeof(DevOp) + 16 * (uint32_t)o.terms.size();
-        if (o.type == H_DENSE)
-            return (uint32_t)sizeof(DevOp) + 16 * (uint32_t)o.terms.size() +
-                   (uint32_t)(dense_b_words(tc_mode) / 32) * mb;
+        if (o.type == H_DENSE) return (uint32_t)sizeof(DevOp) + 16 * (uint32_t)o.terms.size();
         return (uint32_t)sizeof(DevOp) + mb;
     }
 
@@ -624,20 +622,15 @@ struct Encoder {
             // per-pass program budget (same register bits)
             Piece cur{Rs, {}};
             uint32_t cur_bytes = 0;
-            bool cur_dense = false;
             for (const HOp &o : merged) {
                 const uint32_t ob = op_bytes(o);
-                const bool dn = cur_dense || o.type == H_DENSE;
-                const uint32_t cap = dn ? kMaxDensePassProgramBytes : kMaxPassProgramBytes;
-                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > cap)) {
+                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > kMaxPassProgramBytes)) {
                     pieces.push_back(cur);
                     cur.ops.clear();
                     cur_bytes = 0;
-                    cur_dense = false;
                 }
                 cur.ops.push_back(o);
                 cur_bytes += ob;
-                cur_dense = cur_dense || o.type == H_DENSE;
             }
             if (!cur.ops.empty()) pieces.push_back(cur);
         }
@@ -647,24 +640,15 @@ struct Encoder {
             for (const HOp &o : pc.ops) b += op_bytes(o);
             return b;
         };
-        auto piece_dense = [&](const Piece &pc) {
-            for (const HOp &o : pc.ops)
-                if (o.type == H_DENSE) return true;
-            return false;
-        };
         size_t p0 = 0;
         do {
-            // as many pieces as the stage and program limits allow (the larger
-            // budget once a piece with dense ops is in)
+            // as many pieces as the stage and program limits allow
             size_t p1 = p0;
             uint32_t bytes = 0;
-            bool dense = false;
             while (p1 < pieces.size() && (int)(p1 - p0) < kMaxStages) {
                 uint32_t b = piece_bytes(pieces[p1]);
-                const bool dn = dense || piece_dense(pieces[p1]);
-                if (p1 > p0 && bytes + b > (dn ? kMaxDensePassProgramBytes : kMaxPassProgramBytes)) break;
+                if (p1 > p0 && bytes + b > kMaxPassProgramBytes) break;
                 bytes += b;
-                dense = dn;
                 ++p1;
             }
             PassDesc pd;
@@ -827,15 +811,15 @@ struct Encoder {
                                 }
                             d.b = dev < 1e-9 ? 1 : 0;
                         }
-                        d.mat = (uint32_t)(prog.mats.size() / 32);
                         const size_t words = dense_b_words(tc_mode);
-                        // FP64 pool: U itself (2048 doubles), zero-padded to the slots
-                        // the FP32 B parts take
-                        for (size_t k = 0; k < words; ++k)
-                            prog.mats.push_back(k < 2048 ? ((k & 1) ? o.du[k / 2].imag() : o.du[k / 2].real()) : 0.0);
-                        std::vector<float> b(words);
-                        encode_dense_b(o.du.data(), tc_mode, b.data());
-                        prog.dense_b.emplace_back(d.mat, std::move(b));
+                        d.mat = (uint32_t)(prog.dense_pool.size() / words);
+                        for (size_t k = 0; k < 1024; ++k) {
+                            prog.dense_u.push_back(o.du[k].real());
+                            prog.dense_u.push_back(o.du[k].imag());
+                        }
+                        const size_t at = prog.dense_pool.size();
+                        prog.dense_pool.resize(at + words);
+                        encode_dense_b(o.du.data(), tc_mode, prog.dense_pool.data() + at);
                         // the absorbed fixed-bit terms: a per-thread constant phase
                         d.phi0 = to_fixed(o.phi0, false);
                         d.term_begin = (uint32_t)prog.term_mask.size();
@@ -896,7 +880,7 @@ struct Encoder {
             pd.nterm = (uint32_t)prog.term_mask.size() - pd.term0;
             pd.prog_bytes = pd.nops * (uint32_t)sizeof(DevOp) + pd.nmat * mat_bytes + pd.nterm * 16;
             // the kernels reserve exactly this much shared memory for a program
-            if (pd.prog_bytes > ((pd.flags & PF_DENSE) ? kMaxDensePassProgramBytes : kMaxPassProgramBytes))
+            if (pd.prog_bytes > kMaxPassProgramBytes)
                 throw std::logic_error("encoder: pass program exceeds the shared-memory budget");
             pass_ids.push_back((int)prog.passes.size());
             prog.passes.push_back(pd);
@@ -1315,8 +1299,6 @@ void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog)
         if ((st.type == ST_RESTORE && (st.snap < 0 || st.snap >= top)) || (st.type == ST_CHECK && st.snap >= top))
             throw std::logic_error("compile: step snapshot slot out of range");
     prog.matsf.assign(prog.mats.begin(), prog.mats.end());
-    for (const auto &db : prog.dense_b)
-        std::copy(db.second.begin(), db.second.end(), prog.matsf.begin() + 32 * (size_t)db.first);
 }
 
 }  // namespace tusq

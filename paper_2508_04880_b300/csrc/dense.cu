@@ -18,17 +18,15 @@ __global__ void __launch_bounds__(256, 1) dense_check_kernel(const float2 *x, fl
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
-    unsigned char *abase = smem;                 // 64 KiB staging
-    unsigned char *bbase = smem + 65536;         // B parts
-    for (uint32_t i = tid; i < b_bytes / 16; i += blockDim.x)
-        reinterpret_cast<int4 *>(bbase)[i] = reinterpret_cast<const int4 *>(b)[i];
+    unsigned char *abase = smem;                 // 64 KiB: A staging, and B copied to its top
+    (void)b_bytes;
     if (tid == 0) abort_flag = 0;
     float2 a[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) a[i] = x[32 * tid + i];
     dense_setup(&tmem_slot, &mbar, tid);
     DenseCtx c{tmem_slot, smem_u32(&mbar), 0u, err, &abort_flag, 0};
-    dense_apply<MODE>(a, abase, bbase, c, tid, renorm != 0);
+    dense_apply<MODE>(a, abase, b, c, tid, renorm != 0);
 #pragma unroll
     for (int i = 0; i < 32; ++i) y[32 * tid + i] = a[i];
     dense_teardown(c.tmem, tid);
@@ -38,10 +36,10 @@ template <int MODE>
 static cudaError_t launch_check(const float2 *x, float2 *y, const float *b, uint32_t bb, unsigned int *err,
                                 cudaStream_t st) {
     const int renorm = 0;     // the diagnostic checks the raw tensor-core product
-    // staging + B parts + 64 KiB of slack after them, so that a descriptor
-    // read with the leading and stride offsets exchanged would still stay
-    // inside this CTA's allocation
-    const size_t smem = 65536 + bb + 65536;
+    // the 64 KiB area the pass kernel lends a dense op (its tile), plus
+    // 64 KiB of slack after it: a descriptor read with the leading and stride
+    // offsets exchanged would still stay inside this CTA's allocation
+    const size_t smem = 65536 + 65536;
     cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

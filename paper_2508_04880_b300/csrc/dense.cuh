@@ -12,7 +12,7 @@
 //
 // Shared-memory operand layout (no swizzle, K-major canonical form): the K
 // extent is cut into 16-byte chunks (4 TF32 or 8 BF16 values); chunk c of
-// row r sits at base + c * (rows * 16) + r * 16.  In the matrix descriptor
+// row r sits at base + c * (rows * 16) + r * 16 (rows = 128 for A, 64 for B).  In the matrix descriptor
 // the leading-dimension byte offset is the chunk stride (rows * 16) and the
 // stride-dimension byte offset is the distance between 8-row groups (128).
 //
@@ -113,37 +113,45 @@ __device__ __forceinline__ bool dense_wait(DenseCtx &c) {
     return true;
 }
 
-// Write one thread's vector as row `row` of the A operand parts at `abase`.
+// FP32 words of one dense op's B operand parts (device side of dense_b_words).
+__device__ __forceinline__ uint32_t dense_b_words_dev(uint32_t mode) {
+    return (uint32_t)dense_b_parts((int)mode) * dense_b_part_bytes((int)mode) / 4u;
+}
+
+// Write part `part` (0 hi, 1 lo) of one thread's vector as row `row` of an A
+// operand part at `abase`: 16-byte chunks of K at chunk * 2048 + row * 16.
 template <int MODE>
-__device__ __forceinline__ void dense_stage_row(const float2 (&a)[32], unsigned char *abase, int row) {
+__device__ __forceinline__ void dense_stage_part(const float2 (&a)[32], unsigned char *abase, int row, int part) {
     if constexpr (MODE == TUSQ_TC_BF16X3) {
-        // 8 chunks of 8 BF16 per part; part lo follows part hi
+        // 8 chunks of 8 BF16
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            uint32_t hw[4], lw[4];
+            uint32_t w[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float2 v = a[4 * c + q];
-                const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
-                const __nv_bfloat16 lx = __float2bfloat16_rn(v.x - __bfloat162float(hx));
-                const __nv_bfloat16 ly = __float2bfloat16_rn(v.y - __bfloat162float(hy));
-                hw[q] = (uint32_t)__bfloat16_as_ushort(hx) | ((uint32_t)__bfloat16_as_ushort(hy) << 16);
-                lw[q] = (uint32_t)__bfloat16_as_ushort(lx) | ((uint32_t)__bfloat16_as_ushort(ly) << 16);
+                __nv_bfloat16 x = __float2bfloat16_rn(v.x), y = __float2bfloat16_rn(v.y);
+                if (part) {
+                    x = __float2bfloat16_rn(v.x - __bfloat162float(x));
+                    y = __float2bfloat16_rn(v.y - __bfloat162float(y));
+                }
+                w[q] = (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
             }
-            *reinterpret_cast<uint4 *>(abase + c * 2048 + row * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(abase + 16384 + c * 2048 + row * 16) =
-                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            *reinterpret_cast<uint4 *>(abase + c * 2048 + row * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     } else {
-        // 16 chunks of 4 TF32 per part
+        // 16 chunks of 4 TF32
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const float2 v0 = a[2 * c], v1 = a[2 * c + 1];
-            const float h0 = to_tf32(v0.x), h1 = to_tf32(v0.y), h2 = to_tf32(v1.x), h3 = to_tf32(v1.y);
+            float h0 = to_tf32(v0.x), h1 = to_tf32(v0.y), h2 = to_tf32(v1.x), h3 = to_tf32(v1.y);
+            if (part) {
+                h0 = to_tf32(v0.x - h0);
+                h1 = to_tf32(v0.y - h1);
+                h2 = to_tf32(v1.x - h2);
+                h3 = to_tf32(v1.y - h3);
+            }
             *reinterpret_cast<float4 *>(abase + c * 2048 + row * 16) = make_float4(h0, h1, h2, h3);
-            if constexpr (MODE == TUSQ_TC_TF32X3)
-                *reinterpret_cast<float4 *>(abase + 32768 + c * 2048 + row * 16) =
-                    make_float4(to_tf32(v0.x - h0), to_tf32(v0.y - h1), to_tf32(v1.x - h2), to_tf32(v1.y - h3));
         }
     }
 }
@@ -151,16 +159,26 @@ __device__ __forceinline__ void dense_stage_row(const float2 (&a)[32], unsigned 
 // y = U x on every thread's 32 registers, all 256 threads of the CTA taking
 // part (every call site is reached by the whole CTA).  `abase`: 64 KiB of
 // shared memory free for the call (the pass tile, whose amplitudes are held
-// in registers meanwhile); `bbase`: the B parts (hi, then lo) of U.  Two
-// rounds of 128 rows (threads 0-127, then 128-255), each an M = 128, N = 64,
-// K = 64 product per split term into its own 64 TMEM columns.
+// in registers meanwhile); `bsrc`: the op's B operand parts in global memory
+// (hi, then lo), which are copied to the top of that area (cp.async) while
+// the first A rows are written.  Rows go in two halves of 128 (threads 0-127,
+// then 128-255), each an M = 128, N = 64, K = 64 product per split term into
+// its own 64 TMEM columns:
+//   BF16X3: A hi and lo of a half (16 KiB each) at 0 and 16 KiB, B (16 KiB) at
+//           48 KiB: one round per half, products hi.hi + hi.lo + lo.hi;
+//   TF32:   A (32 KiB) at 0, B (16 KiB) at 48 KiB: one round per half;
+//   TF32X3: A hi of a half (32 KiB) at 0 with B (32 KiB) at 32 KiB: hi.hi +
+//           hi.lo, then A lo over it: + lo.hi -- two rounds per half.
 template <int MODE>
-__device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abase, const unsigned char *bbase,
+__device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abase, const float *bsrc,
                                             DenseCtx &c, int tid, bool renorm) {
     constexpr bool kBF = MODE == TUSQ_TC_BF16X3;
-    constexpr uint32_t kApart = dense_a_part_bytes(MODE), kBpart = dense_b_part_bytes(MODE);
+    constexpr uint32_t kBpart = dense_b_part_bytes(MODE);
+    constexpr uint32_t kBbytes = (uint32_t)dense_b_parts(MODE) * kBpart;
+    constexpr uint32_t kBoff = 65536u - kBbytes;
     constexpr int kSteps = kBF ? 4 : 8;            // K = 64 in steps of 16 (BF16) or 8 (TF32)
-    const uint32_t a_s = smem_u32(abase), b_s = smem_u32(bbase);
+    constexpr int kRounds = MODE == TUSQ_TC_TF32X3 ? 2 : 1;   // staging rounds per half
+    const uint32_t a_s = smem_u32(abase), b_s = smem_u32(abase + kBoff);
     const int warp = tid >> 5;
     // *c.abort only changes inside dense_wait, and every read of it follows
     // the barrier after that wait, so all threads see the same value
@@ -174,36 +192,65 @@ __device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abas
         for (int i = 0; i < 32; ++i) nx = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, nx));
     }
     __syncthreads();                               // every thread has gathered its amplitudes
-    for (int rd = 0; rd < 2; ++rd) {
-        const bool mine = (tid >> 7) == rd;
-        if (mine) dense_stage_row<MODE>(a, abase, tid & 127);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && !c.skip_issue) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t idesc = dense_idesc(kBF);
-            const uint32_t d = c.tmem + 64u * rd;
-            // split terms: (A part, B part)
-            constexpr int kTerms = MODE == TUSQ_TC_TF32 ? 1 : 3;
-            const int ap[3] = {0, 0, 1}, bp[3] = {0, 1, 0};
-#pragma unroll
-            for (int t = 0; t < kTerms; ++t)
-#pragma unroll
-                for (int s = 0; s < kSteps; ++s) {
-                    const uint64_t ad = dense_desc(a_s + ap[t] * kApart + s * 4096u, 2048u, 128u);
-                    const uint64_t bd = dense_desc(b_s + bp[t] * kBpart + s * 2048u, 1024u, 128u);
-                    dense_mma(d, ad, bd, idesc, t > 0 || s > 0, kBF);
+    // B: global -> shared, 16 bytes per copy, no register round trip
+    for (uint32_t i = tid; i < kBbytes / 16; i += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(b_s + 16 * i), "l"(bsrc + 4 * i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int h = 0; h < 2; ++h) {
+        const bool mine = (tid >> 7) == h;
+        for (int rd = 0; rd < kRounds; ++rd) {
+            if (mine) {
+                if constexpr (MODE == TUSQ_TC_BF16X3) {
+                    dense_stage_part<MODE>(a, abase, tid & 127, 0);
+                    dense_stage_part<MODE>(a, abase + 16384, tid & 127, 1);
+                } else {
+                    dense_stage_part<MODE>(a, abase, tid & 127, rd);
                 }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
-                         : "memory");
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0 && !c.skip_issue) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t idesc = dense_idesc(kBF);
+                const uint32_t d = c.tmem + 64u * h;
+                // split terms of this round: (A offset, B part)
+                if constexpr (MODE == TUSQ_TC_BF16X3) {
+                    const uint32_t ao[3] = {0u, 0u, 16384u}, bp[3] = {0u, 1u, 0u};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+#pragma unroll
+                        for (int s = 0; s < kSteps; ++s)
+                            dense_mma(d, dense_desc(a_s + ao[t] + s * 4096u, 2048u, 128u),
+                                      dense_desc(b_s + bp[t] * kBpart + s * 2048u, 1024u, 128u), idesc, t > 0 || s > 0,
+                                      true);
+                } else if (MODE == TUSQ_TC_TF32X3 && rd == 0) {
+#pragma unroll
+                    for (int t = 0; t < 2; ++t)
+#pragma unroll
+                        for (int s = 0; s < kSteps; ++s)
+                            dense_mma(d, dense_desc(a_s + s * 4096u, 2048u, 128u),
+                                      dense_desc(b_s + t * kBpart + s * 2048u, 1024u, 128u), idesc, t > 0 || s > 0,
+                                      false);
+                } else {
+                    // TF32 (one product), or TF32X3's lo.hi added to the first round's
+#pragma unroll
+                    for (int s = 0; s < kSteps; ++s)
+                        dense_mma(d, dense_desc(a_s + s * 4096u, 2048u, 128u), dense_desc(b_s + s * 2048u, 1024u, 128u),
+                                  idesc, rd > 0 || s > 0, false);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
+                             : "memory");
+            }
+            dense_wait(c);                         // on timeout: error word and abort flag
+            __syncthreads();
+            if (*c.abort) return;                  // uniform: read after the barrier
         }
-        dense_wait(c);                             // on timeout: error word and abort flag
-        __syncthreads();
-        if (*c.abort) return;                      // uniform: read after the barrier
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (mine) {
             uint32_t r[64];
-            const uint32_t taddr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64u * rd;
+            const uint32_t taddr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64u * h;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "

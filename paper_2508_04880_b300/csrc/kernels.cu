@@ -333,7 +333,8 @@ __device__ __forceinline__ SProg<R> load_program(const PassDesc &d, unsigned cha
 // tb); threads beyond 2^(L-V) only take part in the barriers.
 template <typename R, int V, bool DENSE = false>
 __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const PassDesc &d, const SProg<R> &P,
-                                           int tid, uint64_t tb, DenseCtx *dc = nullptr) {
+                                           int tid, uint64_t tb, DenseCtx *dc = nullptr,
+                                           const float *dpool = nullptr) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
@@ -373,7 +374,7 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
                             }
                             apply_diag<R, V>(a, op, P, gfix, acc);
                         }
-                        const unsigned char *bptr = reinterpret_cast<const unsigned char *>(P.mats + 16 * (op.mat - P.mat0));
+                        const float *bptr = dpool + (size_t)op.mat * dense_b_words_dev(op.sub);
                         unsigned char *stg = reinterpret_cast<unsigned char *>(tile);
                         const bool renorm = op.b != 0;    // U is unitary
                         if (op.sub == TUSQ_TC_TF32X3) dense_apply<TUSQ_TC_TF32X3>(a, stg, bptr, *dc, tid, renorm);
@@ -428,7 +429,8 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
 template <typename R, int V, bool DENSE>
 __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, void *statev, void *snapv, double *acc,
                                           double *partial_out, const SProg<R> &P, unsigned char *smem_raw,
-                                          uint64_t first, uint64_t stride, DenseCtx &dctx) {
+                                          uint64_t first, uint64_t stride, DenseCtx &dctx,
+                                          const float *dpool = nullptr) {
     using C2 = typename C2T<R>::type;
     constexpr int NR = 1 << V;
     constexpr bool kC128 = sizeof(R) == 8;
@@ -483,7 +485,7 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
             for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
-        run_stages<R, V, DENSE>(tile, d, P, tid, tb, DENSE ? &dctx : nullptr);
+        run_stages<R, V, DENSE>(tile, d, P, tid, tb, DENSE ? &dctx : nullptr, dpool);
         if constexpr (DENSE)
             if (*dctx.abort) break;      // a tensor-core wait ran out: stop (uniform after the stage barrier)
         // store + epilogue
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
     }
 
     pass_body<R, V, DENSE>(d, args.src, args.state, args.snap, args.acc, args.partials + 3 * blockIdx.x, P,
-                           smem_raw, blockIdx.x, gridDim.x, dctx);
+                           smem_raw, blockIdx.x, gridDim.x, dctx, args.dpool);
 }
 
 // state <- |0..0>
@@ -710,7 +712,7 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaS
 // Resident CTAs per SM for a pass configuration (for grid sizing); dense:
 // the pass carries tensor-core dense ops (larger program budget).
 int pass_occupancy(int precision, int V, int L, bool dense) {
-    const uint32_t cap = dense ? kMaxDensePassProgramBytes : kMaxPassProgramBytes;
+    const uint32_t cap = kMaxPassProgramBytes;
     if (precision == TUSQ_C128) {
         switch (V) {
         case 1: return occupancy_t<double, 1>(L, cap);

@@ -272,6 +272,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
             a.tphi = (const uint64_t *)at(lay.tphi);
             a.err = nullptr;          // no dense ops here (tc_mode is not used), so nothing waits
             a.dense_skip = 0;
+            a.dpool = nullptr;
             last_grid = grid[s.pass];
             NA_TRY(launch_pass(a, o.precision, std::min(pg.reg_bits, a.d.L), last_grid, st));
             break;

@@ -76,10 +76,12 @@ enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DI
                           CODE_DENSE = 96 };
 
 // Tensor-core dense op (OP_DENSE, code CODE_DENSE, sub = the tc mode): the
-// stage's 32 registers times one 32x32 complex matrix U.  `mat` is its first
-// matrix slot: the FP32 pool holds the B operand parts of U in the kernels'
-// shared-memory layout (dense_b_words(mode) words), the FP64 pool holds U
-// itself (row-major, 2048 doubles) for host-side interpreters.  phi0 and the
+// stage's 32 registers times one 32x32 complex matrix U.  `mat` is its index
+// in the dense pool: Program::dense_pool holds the B operand parts of U in the
+// kernels' shared-memory layout (dense_b_words(mode) words from mat *
+// dense_b_words(mode)), which the kernel copies into the tile's shared memory
+// for the op; Program::dense_u holds U itself (row-major, 2048 doubles from
+// mat * 2048) for host-side interpreters.  phi0 and the
 // csr[0]..csr[1] terms are diagonal terms on fixed bits only: a per-thread
 // constant phase (mu_mask is 0).  b = 1 when U is unitary: each thread's
 // 32-vector then keeps its norm, which the kernel restores after the
@@ -118,9 +120,6 @@ struct StageDesc {
 constexpr int kMaxStageOps = 48;
 constexpr int kMaxDiagTerms = 256;
 constexpr uint32_t kMaxPassProgramBytes = 40 * 1024;
-// A pass with tensor-core dense ops carries their B operands (16 or 32 KiB
-// each) in its program: it may use up to this much (one CTA per SM then).
-constexpr uint32_t kMaxDensePassProgramBytes = 160 * 1024;
 
 enum PassFlags : uint32_t {
     PF_WRITE = 1,          // write the tile back to the state
@@ -179,9 +178,10 @@ struct Program {
     std::vector<DevOp> ops;
     std::vector<double> mats;        // 32 doubles (16 complex) per matrix slot
     std::vector<float> matsf;        // the same slots in FP32 (complex64 kernels)
-    // dense ops: (first slot, FP32 words) written over matsf after the
-    // FP64 -> FP32 conversion of the pool
-    std::vector<std::pair<uint32_t, std::vector<float>>> dense_b;
+    // dense ops: their B operand parts (FP32 words, dense_b_words(mode) per
+    // op) and their matrices U (2048 doubles per op), indexed by DevOp::mat
+    std::vector<float> dense_pool;
+    std::vector<double> dense_u;
     std::vector<uint64_t> term_mask;
     std::vector<uint64_t> term_phi;
     int max_depth = 0;
@@ -211,6 +211,7 @@ struct PassArgs {
     unsigned int *err;    // bit 0 set when a bounded device wait ran out
     int dense_skip;       // test hook: dense ops never issue their tensor-core work
     int pad;
+    const float *dpool;   // B operand parts of the dense ops (Program::dense_pool)
 };
 
 // One job of a batch launch: its steps in the batch's step array (pass,

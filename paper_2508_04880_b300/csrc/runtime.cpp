@@ -53,6 +53,7 @@ struct tusq_exec {
     double *mats = nullptr;
     float *matsf = nullptr;
     uint64_t *tmask = nullptr, *tphi = nullptr;
+    float *dpool = nullptr;          // B operand parts of the dense ops
     std::vector<int> grid_of_pass;
     int max_grid = 1;
     double record_bias = 0.0;
@@ -109,7 +110,7 @@ int dmalloc(T **p, size_t bytes, cudaStream_t st) {
 
 void release(tusq_exec *e) {
     void *bufs[] = {e->state, e->snaps, e->records, e->partials, e->drift_log, e->restore_flag,
-                    e->counters, e->ops, e->mats, e->matsf, e->tmask, e->tphi};
+                    e->counters, e->ops, e->mats, e->matsf, e->tmask, e->tphi, e->dpool};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, e->stream);
     e->state = e->snaps = nullptr;
@@ -120,6 +121,7 @@ void release(tusq_exec *e) {
     e->mats = nullptr;
     e->matsf = nullptr;
     e->tmask = e->tphi = nullptr;
+    e->dpool = nullptr;
 }
 
 }  // namespace
@@ -194,7 +196,7 @@ static void static_info(const Program &pg, size_t amp_bytes, uint64_t dim, tusq_
     info->kernel_launches = launches;
     info->algorithmic_bytes = bytes;
     info->program_bytes = (double)(sizeof(DevOp) * pg.ops.size() + sizeof(double) * pg.mats.size() +
-                                   sizeof(float) * pg.matsf.size() +
+                                   sizeof(float) * (pg.matsf.size() + pg.dense_pool.size()) +
                                    sizeof(uint64_t) * (pg.term_mask.size() + pg.term_phi.size()));
 }
 
@@ -374,6 +376,7 @@ int exec_materialize(tusq_exec *e, cudaStream_t st) {
     ALLOC(e->matsf, sizeof(float) * std::max<size_t>(pg.matsf.size(), 1));
     ALLOC(e->tmask, sizeof(uint64_t) * std::max<size_t>(pg.term_mask.size(), 1));
     ALLOC(e->tphi, sizeof(uint64_t) * std::max<size_t>(pg.term_phi.size(), 1));
+    if (!pg.dense_pool.empty()) ALLOC(e->dpool, sizeof(float) * pg.dense_pool.size());
 #undef ALLOC
     auto up = [&](void *dst, const void *src, size_t bytes) -> int {
         if (!bytes) return TUSQ_OK;
@@ -385,7 +388,8 @@ int exec_materialize(tusq_exec *e, cudaStream_t st) {
         (rc = up(e->mats, pg.mats.data(), sizeof(double) * pg.mats.size())) ||
         (rc = up(e->matsf, pg.matsf.data(), sizeof(float) * pg.matsf.size())) ||
         (rc = up(e->tmask, pg.term_mask.data(), sizeof(uint64_t) * pg.term_mask.size())) ||
-        (rc = up(e->tphi, pg.term_phi.data(), sizeof(uint64_t) * pg.term_phi.size()))) {
+        (rc = up(e->tphi, pg.term_phi.data(), sizeof(uint64_t) * pg.term_phi.size())) ||
+        (rc = up(e->dpool, pg.dense_pool.data(), sizeof(float) * pg.dense_pool.size()))) {
         release(e);
         delete e;
         return rc;
@@ -471,6 +475,7 @@ static int exec_launch_direct(tusq_exec *e, double *probs, cudaStream_t st) {
             a.tphi = e->tphi;
             a.err = reinterpret_cast<unsigned int *>(e->counters + 3);
             a.dense_skip = e->dense_skip;
+            a.dpool = e->dpool;
             last_grid = e->grid_of_pass[s.pass];
             if (e->profiling) CUDA_TRY(cudaEventRecord(e->prof_ev[2 * npass], st));
             CUDA_TRY(launch_pass(a, e->opts.precision, std::min(e->V, a.d.L), last_grid, st));

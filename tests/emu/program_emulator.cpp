@@ -11,7 +11,7 @@
 // per-register fixed-point angles (a Walsh-Hadamard form of the register-mask
 // groups whose phases the kernels apply group by group) and directly from the
 // global index; any mismatch is reported.  Tensor-core dense ops apply the
-// FP64 matrix U the compiler stored beside their B operand parts.
+// FP64 matrix U the compiler stored in the program's dense_u.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -103,9 +103,11 @@ static void run_pass(const Program &pg, const PassDesc &d, std::vector<cd> &stat
                     if (op.type == OP_DENSE) {
                         // U from the FP64 pool (row-major 32x32); its absorbed
                         // fixed-bit terms follow as a per-thread constant phase
+                        const double *u = &pg.dense_u[2048 * (size_t)op.mat];
                         std::vector<cd> y(1 << v, cd(0));
                         for (int r = 0; r < (1 << v); ++r)
-                            for (int c2 = 0; c2 < (1 << v); ++c2) y[r] += M(32 * r + c2) * a[c2];
+                            for (int c2 = 0; c2 < (1 << v); ++c2)
+                                y[r] += cd(u[2 * (32 * r + c2)], u[2 * (32 * r + c2) + 1]) * a[c2];
                         a = y;
                     }
                     if (op.type == OP_DENSE && op.csr[1] == op.csr[0] && op.phi0 == 0) {

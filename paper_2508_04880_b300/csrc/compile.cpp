@@ -280,9 +280,9 @@ std::vector<std::vector<int>> schedule(const std::vector<HOp> &ops, int cap, uin
     return groups;
 }
 
-// Merge neighbouring diagonal ops and neighbouring 1q matrices on the same
-// qubit inside one op list (application order).
-std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
+// Merge neighbouring diagonal ops (unless `diag` is false) and neighbouring
+// 1q matrices on the same qubit inside one op list (application order).
+std::vector<HOp> merge_ops(const std::vector<HOp> &in, bool diag = true) {
     std::vector<HOp> out;
     auto absorb = [](HOp &p, const HOp &o) {
         p.merged.push_back(o.uid);
@@ -293,7 +293,7 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
     for (const HOp &o : in) {
         if (!out.empty()) {
             HOp &p = out.back();
-            if (o.type == H_DIAG && p.type == H_DIAG &&
+            if (diag && o.type == H_DIAG && p.type == H_DIAG &&
                 p.terms.size() + o.terms.size() <= (size_t)kMaxDiagTerms) {
                 p.phi0 += o.phi0;
                 for (auto &t : o.terms) {
@@ -318,6 +318,104 @@ std::vector<HOp> merge_ops(const std::vector<HOp> &in) {
         out.push_back(o);
     }
     return out;
+}
+
+// Move each diagonal op of a pass to the register stage where its terms are
+// cheapest.  A stage applies a term whose qubits are all outside its register
+// bits as one parity per thread added to the thread's constant phase, but a
+// term on register bits as a sweep over the thread's registers for its
+// register-mask group (shared by the terms of one group in the same run).
+// Diagonal ops commute with each other, so an op may sit in any stage from the
+// one of the last non-diagonal op before it on one of its qubits to the one of
+// the first non-diagonal op after it (stage lists are in application order).
+// Rs[s] is stage s's register-bit mask over local bits; local[q] the local
+// bit of global qubit q (-1 outside the window: a tile bit, never a register).
+void place_diagonals(const std::vector<HOp> &ops, std::vector<std::vector<int>> &sched,
+                     const std::vector<uint64_t> &Rs, const int *local) {
+    const int S = (int)sched.size();
+    const int m = (int)ops.size();
+    if (S < 2) return;
+    std::vector<int> stage_of(m, -1);
+    for (int s = 0; s < S; ++s)
+        for (int b : sched[s]) stage_of[b] = s;
+    auto reg_mask = [&](uint64_t qmask, int s) {
+        uint64_t mu = 0;
+        for (uint64_t q = qmask; q; q &= q - 1) {
+            const int l = local[__builtin_ctzll(q)];
+            if (l >= 0 && (Rs[s] >> l & 1)) mu |= 1ULL << l;
+        }
+        return mu;
+    };
+    // per stage: the register-mask groups of its diagonal terms, and how many
+    // diagonal ops it holds
+    std::vector<std::vector<uint64_t>> groups(S);
+    std::vector<int> ndiag(S, 0);
+    auto account = [&](int b, int s, bool add) {
+        ndiag[s] += add ? 1 : -1;
+        auto &g = groups[s];
+        for (const auto &t : ops[b].terms) {
+            const uint64_t mu = reg_mask(t.first, s);
+            if (!mu) continue;
+            if (add) g.push_back(mu);
+            else g.erase(std::find(g.begin(), g.end(), mu));
+        }
+    };
+    // estimated instructions per amplitude of adding op b to stage s
+    constexpr double kFixedTerm = 0.25, kSharedGroup = 0.3, kNewGroup = 2.8, kNewStage = 0.5;
+    auto cost = [&](int b, int s) {
+        double c = ndiag[s] == 0 ? kNewStage : 0.0;
+        std::vector<uint64_t> seen;
+        for (const auto &t : ops[b].terms) {
+            const uint64_t mu = reg_mask(t.first, s);
+            if (!mu) {
+                c += kFixedTerm;
+                continue;
+            }
+            const bool shared = std::find(groups[s].begin(), groups[s].end(), mu) != groups[s].end() ||
+                                std::find(seen.begin(), seen.end(), mu) != seen.end();
+            c += shared ? kSharedGroup : kNewGroup;
+            seen.push_back(mu);
+        }
+        return c;
+    };
+    for (int b = 0; b < m; ++b)
+        if (ops[b].type == H_DIAG) account(b, stage_of[b], true);
+    for (int b = 0; b < m; ++b) {
+        if (ops[b].type != H_DIAG) continue;
+        const uint64_t qm = ops[b].qmask();
+        int lo = 0, hi = S - 1;
+        for (int a = 0; a < m; ++a) {
+            if (ops[a].type == H_DIAG || !(ops[a].qmask() & qm)) continue;
+            if (a < b) lo = std::max(lo, stage_of[a]);
+            else hi = std::min(hi, stage_of[a]);
+        }
+        const int s0 = stage_of[b];
+        if (lo >= hi) continue;
+        account(b, s0, false);
+        int best = s0;
+        double best_cost = cost(b, s0);
+        for (int s = lo; s <= hi; ++s) {
+            if (s == s0) continue;
+            const double c = cost(b, s);
+            if (c < best_cost - 1e-9) {   // strictly cheaper: ties keep the scheduled stage
+                best = s;
+                best_cost = c;
+            }
+        }
+        account(b, best, true);
+        if (best == s0) continue;
+        auto &from = sched[s0];
+        from.erase(std::find(from.begin(), from.end(), b));
+        // a later non-diagonal op on its qubits in the new stage (best == hi):
+        // before the stage's ops; otherwise after them (best == lo may hold an
+        // earlier one)
+        bool later_here = false;
+        for (int a : sched[best])
+            if (a > b && ops[a].type != H_DIAG && (ops[a].qmask() & qm)) later_here = true;
+        if (later_here) sched[best].insert(sched[best].begin(), b);
+        else sched[best].push_back(b);
+        stage_of[b] = best;
+    }
 }
 
 // ------------------------------------------------------------- encoding
@@ -420,6 +518,7 @@ struct Encoder {
     int V;
     int Lmax;
     bool lookahead = true;
+    bool place_diag = true;     // move diagonal ops to their cheapest register stage
     int tc_mode = TUSQ_TC_NONE;
 
     // Program bytes of one op in shared memory.
@@ -559,7 +658,8 @@ struct Encoder {
         int local[64];
         for (int i = 0; i < 64; ++i) local[i] = -1;
         for (int i = 0; i < L; ++i) local[win[i]] = i;
-        std::vector<HOp> ops = merge_ops(ops_in);
+        // diagonal gates stay separate ops until their stages are chosen
+        std::vector<HOp> ops = merge_ops(ops_in, false);
         // stage scheduling over local bits
         auto lq = [&](const HOp &o) -> uint64_t {
             if (o.type == H_DIAG) return 0;
@@ -571,6 +671,15 @@ struct Encoder {
         std::vector<uint64_t> swin;
         std::vector<std::vector<int>> sched;
         if (!ops.empty()) sched = schedule(ops, v, 0, lq, &swin, lookahead);
+        // each stage's register bits: its window filled up to v with the
+        // highest unused local bits (the encoding below uses the same rule)
+        std::vector<uint64_t> Rfill(sched.size());
+        for (size_t s = 0; s < sched.size(); ++s) {
+            uint64_t R = swin[s];
+            for (int b = L - 1; b >= 0 && __builtin_popcountll(R) < v; --b) R |= 1ULL << b;
+            Rfill[s] = R;
+        }
+        if (place_diag) place_diagonals(ops, sched, Rfill, local);
         // inside a stage, order the ops so that every diagonal op that is ready
         // at the same time is applied together (alternately all ready diagonal
         // ops, then all ready matrix ops), and merge neighbours: each diagonal
@@ -614,8 +723,7 @@ struct Encoder {
             std::vector<HOp> merged = merge_ops(ordered);
             // the register bits the stage will use (filled up to v with the
             // highest unused local bits, as the encoding below does)
-            uint64_t Rs = swin[s];
-            for (int b = L - 1; b >= 0 && __builtin_popcountll(Rs) < v; --b) Rs |= 1ULL << b;
+            const uint64_t Rs = Rfill[s];
             if (tc_mode != TUSQ_TC_NONE && !c128 && L == kDenseTileBits && v == kRegBitsC64)
                 merged = densify(merged, Rs, win);
             // cut into pieces of at most kMaxStageOps ops and at most the

@@ -668,6 +668,11 @@ struct Encoder {
             return m;
         };
         const int v = std::min(V, L);
+        // program budget: a pass that may carry dense ops keeps room for the B
+        // region (one dense op's B parts) at the top of its program area
+        const bool may_dense = tc_mode != TUSQ_TC_NONE && !c128 && L == kDenseTileBits && v == kRegBitsC64;
+        const uint32_t dense_region = may_dense ? 4u * (uint32_t)dense_b_words(tc_mode) : 0u;
+        const uint32_t budget = kMaxPassProgramBytes - dense_region;
         std::vector<uint64_t> swin;
         std::vector<std::vector<int>> sched;
         if (!ops.empty()) sched = schedule(ops, v, 0, lq, &swin, lookahead);
@@ -724,15 +729,14 @@ struct Encoder {
             // the register bits the stage will use (filled up to v with the
             // highest unused local bits, as the encoding below does)
             const uint64_t Rs = Rfill[s];
-            if (tc_mode != TUSQ_TC_NONE && !c128 && L == kDenseTileBits && v == kRegBitsC64)
-                merged = densify(merged, Rs, win);
+            if (may_dense) merged = densify(merged, Rs, win);
             // cut into pieces of at most kMaxStageOps ops and at most the
             // per-pass program budget (same register bits)
             Piece cur{Rs, {}};
             uint32_t cur_bytes = 0;
             for (const HOp &o : merged) {
                 const uint32_t ob = op_bytes(o);
-                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > kMaxPassProgramBytes)) {
+                if (!cur.ops.empty() && ((int)cur.ops.size() >= kMaxStageOps || cur_bytes + ob > budget)) {
                     pieces.push_back(cur);
                     cur.ops.clear();
                     cur_bytes = 0;
@@ -755,7 +759,7 @@ struct Encoder {
             uint32_t bytes = 0;
             while (p1 < pieces.size() && (int)(p1 - p0) < kMaxStages) {
                 uint32_t b = piece_bytes(pieces[p1]);
-                if (p1 > p0 && bytes + b > kMaxPassProgramBytes) break;
+                if (p1 > p0 && bytes + b > budget) break;
                 bytes += b;
                 ++p1;
             }
@@ -969,8 +973,15 @@ struct Encoder {
                 }
                 sd.op_count = (uint32_t)(prog.ops.size() - sd.op_begin);
             }
-            for (uint32_t k = pd.op0; k < (uint32_t)prog.ops.size(); ++k)
-                if (prog.ops[k].type == OP_DENSE) pd.flags |= PF_DENSE;
+            // dense ops: each names the next one's pool index (cyclically)
+            {
+                std::vector<uint32_t> dk;
+                for (uint32_t k = pd.op0; k < (uint32_t)prog.ops.size(); ++k)
+                    if (prog.ops[k].type == OP_DENSE) dk.push_back(k);
+                for (size_t i = 0; i < dk.size(); ++i)
+                    prog.ops[dk[i]].a = (int32_t)prog.ops[dk[(i + 1) % dk.size()]].mat;
+                if (!dk.empty()) pd.flags |= PF_DENSE | ((uint32_t)tc_mode << kDenseModeShift);
+            }
             if (Kpass != cd(1.0, 0.0)) {
                 // the scalar goes on the first stage that multiplies by a
                 // per-thread phase anyway (it has a diagonal op), else on the last
@@ -987,6 +998,7 @@ struct Encoder {
             pd.nmat = (uint32_t)(prog.mats.size() / 32) - pd.mat0;
             pd.nterm = (uint32_t)prog.term_mask.size() - pd.term0;
             pd.prog_bytes = pd.nops * (uint32_t)sizeof(DevOp) + pd.nmat * mat_bytes + pd.nterm * 16;
+            if (pd.flags & PF_DENSE) pd.prog_bytes += dense_region;
             // the kernels reserve exactly this much shared memory for a program
             if (pd.prog_bytes > kMaxPassProgramBytes)
                 throw std::logic_error("encoder: pass program exceeds the shared-memory budget");

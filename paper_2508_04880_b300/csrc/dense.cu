@@ -18,15 +18,16 @@ __global__ void __launch_bounds__(256, 1) dense_check_kernel(const float2 *x, fl
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
-    unsigned char *abase = smem;                 // 64 KiB: A staging, and B copied to its top
-    (void)b_bytes;
+    unsigned char *abase = smem;                 // 64 KiB: A staging (the pass kernel's tile)
+    const uint32_t bsm = smem_u32(smem + 65536); // the B region after it
     if (tid == 0) abort_flag = 0;
+    dense_copy_b(bsm, b, b_bytes, tid, blockDim.x);
     float2 a[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) a[i] = x[32 * tid + i];
     dense_setup(&tmem_slot, &mbar, tid);
-    DenseCtx c{tmem_slot, smem_u32(&mbar), 0u, err, &abort_flag, 0};
-    dense_apply<MODE>(a, abase, b, c, tid, renorm != 0);
+    DenseCtx c{tmem_slot, smem_u32(&mbar), 0u, err, &abort_flag, 0, bsm};
+    dense_apply<MODE>(a, abase, nullptr, c, tid, renorm != 0);
 #pragma unroll
     for (int i = 0; i < 32; ++i) y[32 * tid + i] = a[i];
     dense_teardown(c.tmem, tid);
@@ -36,9 +37,10 @@ template <int MODE>
 static cudaError_t launch_check(const float2 *x, float2 *y, const float *b, uint32_t bb, unsigned int *err,
                                 cudaStream_t st) {
     const int renorm = 0;     // the diagnostic checks the raw tensor-core product
-    // the 64 KiB area the pass kernel lends a dense op (its tile), plus
-    // 64 KiB of slack after it: a descriptor read with the leading and stride
-    // offsets exchanged would still stay inside this CTA's allocation
+    // the 64 KiB area the pass kernel lends a dense op (its tile), then the
+    // B region (at most 32 KiB) and slack up to 128 KiB: a descriptor read
+    // with the leading and stride offsets exchanged would still stay inside
+    // this CTA's allocation
     const size_t smem = 65536 + 65536;
     cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

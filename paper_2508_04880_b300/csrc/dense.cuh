@@ -87,6 +87,7 @@ struct DenseCtx {
     unsigned int *err;      // device error word (bit 0: a bounded wait ran out)
     int *abort;             // shared flag: stop the CTA's work after a timeout
     int skip_issue;         // test hook: never issue the MMAs (the wait runs out)
+    uint32_t bsm = 0;       // shared address of the B region (one dense op's B parts)
 };
 
 // Wait for the mbarrier phase with a bound of ~1 s of SM clock; on timeout
@@ -156,30 +157,43 @@ __device__ __forceinline__ void dense_stage_part(const float2 (&a)[32], unsigned
     }
 }
 
+// Copy one dense op's B operand parts (`bytes`, hi then lo) from global
+// memory to the CTA's B region at shared address bsm: 16-byte cp.async
+// copies spread over the CTA's threads, one commit group per thread.
+__device__ __forceinline__ void dense_copy_b(uint32_t bsm, const float *src, uint32_t bytes, int tid,
+                                             int nthr) {
+    for (uint32_t i = tid; i < bytes / 16u; i += nthr)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bsm + 16u * i), "l"(src + 4u * i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // y = U x on every thread's 32 registers, all 256 threads of the CTA taking
 // part (every call site is reached by the whole CTA).  `abase`: 64 KiB of
 // shared memory free for the call (the pass tile, whose amplitudes are held
-// in registers meanwhile); `bsrc`: the op's B operand parts in global memory
-// (hi, then lo), which are copied to the top of that area (cp.async) while
-// the first A rows are written.  Rows go in two halves of 128 (threads 0-127,
-// then 128-255), each an M = 128, N = 64, K = 64 product per split term into
-// its own 64 TMEM columns:
-//   BF16X3: A hi and lo of a half (16 KiB each) at 0 and 16 KiB, B (16 KiB) at
-//           48 KiB: one round per half, products hi.hi + hi.lo + lo.hi;
-//   TF32:   A (32 KiB) at 0, B (16 KiB) at 48 KiB: one round per half;
-//   TF32X3: A hi of a half (32 KiB) at 0 with B (32 KiB) at 32 KiB: hi.hi +
-//           hi.lo, then A lo over it: + lo.hi -- two rounds per half.
+// in registers meanwhile), which takes the A operand of all 256 rows: thread
+// t writes row t & 127 of half t >> 7, and each half is an M = 128, N = 64,
+// K = 64 product per split term into its own 64 TMEM columns.  This op's B
+// parts are already on their way to the B region (c.bsm: copied by an
+// earlier dense_copy_b); once its products are done the region is free and
+// `bnext` (the next dense op's B parts, or null when the region already
+// holds them) is copied in behind the read-out.
+//   BF16X3: A hi of both halves (2 x 16 KiB) then A lo (2 x 16 KiB); one
+//           round, products hi.hi + hi.lo + lo.hi;
+//   TF32:   A of both halves (2 x 32 KiB); one round;
+//   TF32X3: A hi of both halves (2 x 32 KiB): hi.hi + hi.lo, then A lo over
+//           it: + lo.hi -- two rounds.
 template <int MODE>
-__device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abase, const float *bsrc,
+__device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abase, const float *bnext,
                                             DenseCtx &c, int tid, bool renorm) {
     constexpr bool kBF = MODE == TUSQ_TC_BF16X3;
+    constexpr uint32_t kApart = dense_a_part_bytes(MODE);     // one half (128 rows) of one part
     constexpr uint32_t kBpart = dense_b_part_bytes(MODE);
     constexpr uint32_t kBbytes = (uint32_t)dense_b_parts(MODE) * kBpart;
-    constexpr uint32_t kBoff = 65536u - kBbytes;
     constexpr int kSteps = kBF ? 4 : 8;            // K = 64 in steps of 16 (BF16) or 8 (TF32)
-    constexpr int kRounds = MODE == TUSQ_TC_TF32X3 ? 2 : 1;   // staging rounds per half
-    const uint32_t a_s = smem_u32(abase), b_s = smem_u32(abase + kBoff);
-    const int warp = tid >> 5;
+    constexpr int kRounds = MODE == TUSQ_TC_TF32X3 ? 2 : 1;
+    const uint32_t a_s = smem_u32(abase), b_s = c.bsm;
+    const int warp = tid >> 5, half = tid >> 7, row = tid & 127;
     // *c.abort only changes inside dense_wait, and every read of it follows
     // the barrier after that wait, so all threads see the same value
     if (*c.abort) return;
@@ -192,98 +206,92 @@ __device__ __forceinline__ void dense_apply(float2 (&a)[32], unsigned char *abas
         for (int i = 0; i < 32; ++i) nx = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, nx));
     }
     __syncthreads();                               // every thread has gathered its amplitudes
-    // B: global -> shared, 16 bytes per copy, no register round trip
-    for (uint32_t i = tid; i < kBbytes / 16; i += blockDim.x)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(b_s + 16 * i), "l"(bsrc + 4 * i)
-                     : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int h = 0; h < 2; ++h) {
-        const bool mine = (tid >> 7) == h;
-        for (int rd = 0; rd < kRounds; ++rd) {
-            if (mine) {
-                if constexpr (MODE == TUSQ_TC_BF16X3) {
-                    dense_stage_part<MODE>(a, abase, tid & 127, 0);
-                    dense_stage_part<MODE>(a, abase + 16384, tid & 127, 1);
-                } else {
-                    dense_stage_part<MODE>(a, abase, tid & 127, rd);
-                }
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0 && !c.skip_issue) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = dense_idesc(kBF);
+    dense_stage_part<MODE>(a, abase + half * kApart, row, 0);
+    if constexpr (kBF) dense_stage_part<MODE>(a, abase + 2 * kApart + half * kApart, row, 1);
+    for (int rd = 0; rd < kRounds; ++rd) {
+        if (rd > 0) dense_stage_part<MODE>(a, abase + half * kApart, row, 1);   // TF32X3: A lo over A hi
+        asm volatile("cp.async.wait_all;" ::: "memory");            // this op's B parts
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !c.skip_issue) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = dense_idesc(kBF);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
                 const uint32_t d = c.tmem + 64u * h;
-                // split terms of this round: (A offset, B part)
+                const uint32_t ah = a_s + h * kApart;
                 if constexpr (MODE == TUSQ_TC_BF16X3) {
-                    const uint32_t ao[3] = {0u, 0u, 16384u}, bp[3] = {0u, 1u, 0u};
+                    // (A part offset, B part): hi.hi, hi.lo, lo.hi
+                    const uint32_t ao[3] = {0u, 0u, 2 * kApart}, bp[3] = {0u, 1u, 0u};
 #pragma unroll
                     for (int t = 0; t < 3; ++t)
 #pragma unroll
                         for (int s = 0; s < kSteps; ++s)
-                            dense_mma(d, dense_desc(a_s + ao[t] + s * 4096u, 2048u, 128u),
-                                      dense_desc(b_s + bp[t] * kBpart + s * 2048u, 1024u, 128u), idesc, t > 0 || s > 0,
-                                      true);
+                            dense_mma(d, dense_desc(ah + ao[t] + s * 4096u, 2048u, 128u),
+                                      dense_desc(b_s + bp[t] * kBpart + s * 2048u, 1024u, 128u), idesc,
+                                      t > 0 || s > 0, true);
                 } else if (MODE == TUSQ_TC_TF32X3 && rd == 0) {
 #pragma unroll
                     for (int t = 0; t < 2; ++t)
 #pragma unroll
                         for (int s = 0; s < kSteps; ++s)
-                            dense_mma(d, dense_desc(a_s + s * 4096u, 2048u, 128u),
-                                      dense_desc(b_s + t * kBpart + s * 2048u, 1024u, 128u), idesc, t > 0 || s > 0,
-                                      false);
+                            dense_mma(d, dense_desc(ah + s * 4096u, 2048u, 128u),
+                                      dense_desc(b_s + t * kBpart + s * 2048u, 1024u, 128u), idesc,
+                                      t > 0 || s > 0, false);
                 } else {
                     // TF32 (one product), or TF32X3's lo.hi added to the first round's
 #pragma unroll
                     for (int s = 0; s < kSteps; ++s)
-                        dense_mma(d, dense_desc(a_s + s * 4096u, 2048u, 128u), dense_desc(b_s + s * 2048u, 1024u, 128u),
+                        dense_mma(d, dense_desc(ah + s * 4096u, 2048u, 128u), dense_desc(b_s + s * 2048u, 1024u, 128u),
                                   idesc, rd > 0 || s > 0, false);
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
-                             : "memory");
             }
-            dense_wait(c);                         // on timeout: error word and abort flag
-            __syncthreads();
-            if (*c.abort) return;                  // uniform: read after the barrier
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
+                         : "memory");
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (mine) {
-            uint32_t r[64];
-            const uint32_t taddr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64u * h;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
-                "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
-                "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                  "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                  "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                  "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]),
-                  "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]),
-                  "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-                  "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-                  "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]),
-                  "=r"(r[63])
-                : "r"(taddr)
-                : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int i = 0; i < 32; ++i) a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-            if (renorm) {
-                float ny = 0.f;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) ny = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, ny));
-                const float sc = ny > 0.f ? sqrtf(nx / ny) : 1.f;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) a[i] = make_float2(a[i].x * sc, a[i].y * sc);
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        dense_wait(c);                             // on timeout: error word and abort flag
+        __syncthreads();
+        if (*c.abort) return;                      // uniform: read after the barrier
     }
-    __syncthreads();                               // the staging area may be overwritten again
+    // the products are done: the B region is free for the next dense op's parts
+    if (bnext) dense_copy_b(b_s, bnext, kBbytes, tid, blockDim.x);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+        uint32_t r[64];
+        const uint32_t taddr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64u * half;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+            "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+            "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]),
+              "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]),
+              "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+              "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]),
+              "=r"(r[63])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    }
+    if (renorm) {
+        float ny = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) ny = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, ny));
+        const float sc = ny > 0.f ? sqrtf(nx / ny) : 1.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) a[i] = make_float2(a[i].x * sc, a[i].y * sc);
+    }
+    // the next write of the TMEM columns (the next dense op's products) is
+    // issued after a CTA barrier, which this fence orders the read-out before
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
 // Set-up by the whole CTA: warp 0 allocates 128 TMEM columns (address
@@ -303,8 +311,10 @@ __device__ __forceinline__ void dense_setup(uint32_t *tmem_slot, uint64_t *mbar,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Tear-down by the whole CTA after its last dense op: warp 0 frees the TMEM.
+// Tear-down by the whole CTA after its last dense op: its B copies are
+// waited for and warp 0 frees the TMEM.
 __device__ __forceinline__ void dense_teardown(uint32_t tmem, int tid) {
+    asm volatile("cp.async.wait_all;" ::: "memory");   // a prefetched B the CTA did not use
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid < 32) {

@@ -331,7 +331,7 @@ __device__ __forceinline__ SProg<R> load_program(const PassDesc &d, unsigned cha
 
 // The register stages of one pass on one tile in shared memory (tile bits
 // tb); threads beyond 2^(L-V) only take part in the barriers.
-template <typename R, int V, bool DENSE = false>
+template <typename R, int V, int TC = 0>
 __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const PassDesc &d, const SProg<R> &P,
                                            int tid, uint64_t tb, DenseCtx *dc = nullptr,
                                            const float *dpool = nullptr) {
@@ -360,11 +360,11 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
             typename Phase<R>::U acc = 0;     // the stage's per-thread constant phase
             for (uint32_t k = 0; k < sd.op_count; ++k) {
                 const DevOp &op = P.ops[sd.op_begin - P.op0 + k];
-                if (DENSE && op.code == CODE_DENSE) {
+                if (TC != 0 && op.code == CODE_DENSE) {
                     // tensor cores: the stage's thread-independent run as one 32x32
                     // matrix (every thread of the CTA takes part); its fixed-bit
                     // terms join the per-thread constant phase
-                    if constexpr (DENSE && sizeof(R) == 4 && V == 5) {
+                    if constexpr (TC != 0 && sizeof(R) == 4 && V == 5) {
                         if (op.csr[1] > op.csr[0] || op.phi0 != 0) {
                             if (!have_gfix) {
                                 gfix = tb;
@@ -374,12 +374,14 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
                             }
                             apply_diag<R, V>(a, op, P, gfix, acc);
                         }
-                        const float *bptr = dpool + (size_t)op.mat * dense_b_words_dev(op.sub);
+                        // op.a: the pass's next dense op (cyclically, the next tile's
+                        // first), whose B parts follow into the B region
+                        const float *bnext = op.a != (int32_t)op.mat
+                                                 ? dpool + (size_t)op.a * dense_b_words_dev(op.sub)
+                                                 : nullptr;
                         unsigned char *stg = reinterpret_cast<unsigned char *>(tile);
                         const bool renorm = op.b != 0;    // U is unitary
-                        if (op.sub == TUSQ_TC_TF32X3) dense_apply<TUSQ_TC_TF32X3>(a, stg, bptr, *dc, tid, renorm);
-                        else if (op.sub == TUSQ_TC_BF16X3) dense_apply<TUSQ_TC_BF16X3>(a, stg, bptr, *dc, tid, renorm);
-                        else dense_apply<TUSQ_TC_TF32>(a, stg, bptr, *dc, tid, renorm);
+                        dense_apply<TC>(a, stg, bnext, *dc, tid, renorm);   // op.sub == TC
                     }
                 } else if (op.code != CODE_DIAG) {
                     apply_matrix_op<V, R>(a, op, P);
@@ -426,7 +428,7 @@ __device__ __forceinline__ void run_stages(typename C2T<R>::type *tile, const Pa
 // accumulation, partial sums of the norm and checksum into partial_out[0..2]
 // when the pass reduces).  The pass's program is in shared memory (P); the
 // first statement of the tile loop waits for it.
-template <typename R, int V, bool DENSE>
+template <typename R, int V, int TC>
 __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, void *statev, void *snapv, double *acc,
                                           double *partial_out, const SProg<R> &P, unsigned char *smem_raw,
                                           uint64_t first, uint64_t stride, DenseCtx &dctx,
@@ -485,8 +487,8 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
             for (int i = 0; i < NROW; ++i) dst[(sthr ^ d.srow[i]) >> 1] = buf[i];
         }
         __syncthreads();
-        run_stages<R, V, DENSE>(tile, d, P, tid, tb, DENSE ? &dctx : nullptr, dpool);
-        if constexpr (DENSE)
+        run_stages<R, V, TC>(tile, d, P, tid, tb, TC != 0 ? &dctx : nullptr, dpool);
+        if constexpr (TC != 0)
             if (*dctx.abort) break;      // a tensor-core wait ran out: stop (uniform after the stage barrier)
         // store + epilogue
         float pn = 0.f, pr = 0.f, pi = 0.f;
@@ -546,7 +548,7 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
         }
         __syncthreads();
     }
-    if constexpr (DENSE) dense_teardown(dctx.tmem, tid);
+    if constexpr (TC != 0) dense_teardown(dctx.tmem, tid);
     if (flags & PF_REDUCE) {
         // fixed-order block reduction: warp shuffles, then thread 0
         __shared__ double wsum[3][32];
@@ -568,9 +570,9 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
     }
 }
 
-// DENSE: the instantiation for passes with tensor-core dense ops (complex64,
-// V = 5); the others carry none of that code.
-template <typename R, int V, bool DENSE = false>
+// TC: the tc mode of the instantiation for passes with tensor-core dense ops
+// (complex64, V = 5; one per mode); TC = 0 carries none of that code.
+template <typename R, int V, int TC = 0>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const __grid_constant__ PassArgs args) {
     using C2 = typename C2T<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
                                        args.tmask, args.tphi, tid, blockDim.x);
     // tensor-core dense ops: 128 TMEM columns and a completion mbarrier
     DenseCtx dctx{0u, 0u, 0u, args.err, nullptr, args.dense_skip};
-    if constexpr (DENSE) {
+    if constexpr (TC != 0) {
         __shared__ uint32_t s_tmem;
         __shared__ __align__(8) uint64_t s_mbar;
         __shared__ int s_abort;
@@ -589,13 +591,23 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         // dense passes do nothing (the result is void and reported as a timeout)
         if (*args.err) return;
         if (tid == 0) s_abort = 0;
+        // the B region is the top of the program area; the pass's first dense
+        // op's B parts are copied there now, each later op's by the one before
+        const DevOp *gops = args.ops + d.op0;
+        for (uint32_t k = 0; k < d.nops; ++k) {
+            if (gops[k].code != CODE_DENSE) continue;
+            const uint32_t words = dense_b_words_dev(gops[k].sub);
+            dctx.bsm = smem_u32(smem_raw + (sizeof(C2) << d.L) + d.prog_bytes - 4u * words);
+            dense_copy_b(dctx.bsm, args.dpool + (size_t)gops[k].mat * words, 4u * words, tid, blockDim.x);
+            break;
+        }
         dense_setup(&s_tmem, &s_mbar, tid);
         dctx.tmem = s_tmem;
         dctx.mbar = smem_u32(&s_mbar);
         dctx.abort = &s_abort;
     }
 
-    pass_body<R, V, DENSE>(d, args.src, args.state, args.snap, args.acc, args.partials + 3 * blockIdx.x, P,
+    pass_body<R, V, TC>(d, args.src, args.state, args.snap, args.acc, args.partials + 3 * blockIdx.x, P,
                            smem_raw, blockIdx.x, gridDim.x, dctx, args.dpool);
 }
 
@@ -658,33 +670,33 @@ __global__ void restore_kernel(C2 *state, const C2 *snap, uint64_t dim, const in
 
 // Allow the dynamic shared memory a pass tile needs (above the 48 KB
 // default); returns the attribute call's own status.
-template <typename R, int V, bool DENSE = false>
+template <typename R, int V, int TC = 0>
 static cudaError_t allow_smem(size_t smem) {
     static size_t allowed = 48 * 1024;
     if (smem <= allowed) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, V, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, V, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) allowed = smem;
     return e;
 }
 
-template <typename R, int V, bool DENSE = false>
+template <typename R, int V, int TC = 0>
 static cudaError_t launch_pass_t(const PassArgs &a, int grid, cudaStream_t st) {
     const size_t smem = ((sizeof(R) * 2) << a.d.L) + a.d.prog_bytes;
     const int threads = 1 << (a.d.L - V);
-    cudaError_t e = allow_smem<R, V, DENSE>(smem);
+    cudaError_t e = allow_smem<R, V, TC>(smem);
     if (e != cudaSuccess) return e;
-    pass_kernel<R, V, DENSE><<<grid, threads, smem, st>>>(a);
+    pass_kernel<R, V, TC><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R, int V, bool DENSE = false>
+template <typename R, int V, int TC = 0>
 static int occupancy_t(int L, uint32_t prog_cap) {
     const size_t smem = ((sizeof(R) * 2) << L) + prog_cap;
     const int threads = 1 << (L - V);
     int nb = 0;
-    if (allow_smem<R, V, DENSE>(smem) != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R, V, DENSE>, threads, smem) != cudaSuccess)
+    if (allow_smem<R, V, TC>(smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R, V, TC>, threads, smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
@@ -704,14 +716,18 @@ cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaS
     case 3: return launch_pass_t<float, 3>(a, grid, st);
     case 4: return launch_pass_t<float, 4>(a, grid, st);
     default:
-        if (a.d.flags & PF_DENSE) return launch_pass_t<float, 5, true>(a, grid, st);
-        return launch_pass_t<float, 5>(a, grid, st);
+        switch (pass_dense_mode(a.d.flags)) {
+        case TUSQ_TC_TF32X3: return launch_pass_t<float, 5, TUSQ_TC_TF32X3>(a, grid, st);
+        case TUSQ_TC_BF16X3: return launch_pass_t<float, 5, TUSQ_TC_BF16X3>(a, grid, st);
+        case TUSQ_TC_TF32: return launch_pass_t<float, 5, TUSQ_TC_TF32>(a, grid, st);
+        default: return launch_pass_t<float, 5>(a, grid, st);
+        }
     }
 }
 
-// Resident CTAs per SM for a pass configuration (for grid sizing); dense:
-// the pass carries tensor-core dense ops (larger program budget).
-int pass_occupancy(int precision, int V, int L, bool dense) {
+// Resident CTAs per SM for a pass configuration (for grid sizing); tc: the
+// tc mode of the pass's tensor-core dense ops (0: none).
+int pass_occupancy(int precision, int V, int L, int tc) {
     const uint32_t cap = kMaxPassProgramBytes;
     if (precision == TUSQ_C128) {
         switch (V) {
@@ -726,7 +742,13 @@ int pass_occupancy(int precision, int V, int L, bool dense) {
     case 2: return occupancy_t<float, 2>(L, cap);
     case 3: return occupancy_t<float, 3>(L, cap);
     case 4: return occupancy_t<float, 4>(L, cap);
-    default: return dense ? occupancy_t<float, 5, true>(L, cap) : occupancy_t<float, 5>(L, cap);
+    default:
+        switch (tc) {
+        case TUSQ_TC_TF32X3: return occupancy_t<float, 5, TUSQ_TC_TF32X3>(L, cap);
+        case TUSQ_TC_BF16X3: return occupancy_t<float, 5, TUSQ_TC_BF16X3>(L, cap);
+        case TUSQ_TC_TF32: return occupancy_t<float, 5, TUSQ_TC_TF32>(L, cap);
+        default: return occupancy_t<float, 5>(L, cap);
+        }
     }
 }
 

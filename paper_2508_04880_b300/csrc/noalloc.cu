@@ -25,7 +25,7 @@
 namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
 cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st);
-int pass_occupancy(int precision, int V, int L, bool dense);
+int pass_occupancy(int precision, int V, int L, int tc);
 cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
                             int is_check, double *drift_log, int check, int *restore_flag,
@@ -203,7 +203,7 @@ extern "C" int tusq_run_noalloc(const tusq_plan_t *p, const tusq_run_opts *opts,
         for (size_t i = 0; i < pg.passes.size(); ++i) {
             const PassDesc &d = pg.passes[i];
             int V = std::min(pg.reg_bits, d.L);
-            if (!occ[d.L]) occ[d.L] = pass_occupancy(o.precision, V, d.L, false);
+            if (!occ[d.L]) occ[d.L] = pass_occupancy(o.precision, V, d.L, 0);
             uint64_t g = std::min<uint64_t>(d.ntiles, (uint64_t)nsm * occ[d.L]);
             grid[i] = (int)std::max<uint64_t>(g, 1);
             max_grid = std::max(max_grid, grid[i]);

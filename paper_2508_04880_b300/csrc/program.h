@@ -79,8 +79,13 @@ enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DI
 // stage's 32 registers times one 32x32 complex matrix U.  `mat` is its index
 // in the dense pool: Program::dense_pool holds the B operand parts of U in the
 // kernels' shared-memory layout (dense_b_words(mode) words from mat *
-// dense_b_words(mode)), which the kernel copies into the tile's shared memory
-// for the op; Program::dense_u holds U itself (row-major, 2048 doubles from
+// dense_b_words(mode)), which the kernel copies into the pass's B region (the
+// last 4 dense_b_words(mode) bytes of PassDesc::prog_bytes, which count it):
+// the pass's first dense op's at kernel start, every later one's as soon as
+// the op before it is done, so that the copy runs behind other work.  `a` is
+// the pool index of the dense op that follows in the pass, cyclically (the
+// first op of the next tile after the last); a == mat: the region already
+// holds it.  Program::dense_u holds U itself (row-major, 2048 doubles from
 // mat * 2048) for host-side interpreters.  phi0 and the
 // csr[0]..csr[1] terms are diagonal terms on fixed bits only: a per-thread
 // constant phase (mu_mask is 0).  b = 1 when U is unitary: each thread's
@@ -128,6 +133,12 @@ enum PassFlags : uint32_t {
     PF_REDUCE = 8,         // partial sums of |psi|^2 and sum h(x) psi_x
     PF_DENSE = 16,         // has tensor-core dense ops (TMEM is allocated)
 };
+// A PF_DENSE pass holds its dense ops' tc mode (tusq_tc_mode) in flag bits
+// 8-9: the kernels are instantiated once per mode.
+constexpr int kDenseModeShift = 8;
+TUSQ_HD constexpr int pass_dense_mode(uint32_t flags) {
+    return (flags & PF_DENSE) ? (int)((flags >> kDenseModeShift) & 3u) : 0;
+}
 
 struct PassDesc {
     int32_t L;             // tile = 2^L amplitudes

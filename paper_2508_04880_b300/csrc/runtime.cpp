@@ -16,7 +16,7 @@ namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
 
 cudaError_t launch_pass(const PassArgs &a, int precision, int V, int grid, cudaStream_t st);
-int pass_occupancy(int precision, int V, int L, bool dense);
+int pass_occupancy(int precision, int V, int L, int tc);
 cudaError_t launch_init(void *state, int precision, uint64_t dim, int nsm, cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int nparts, double *records, int depth,
                             int is_check, double *drift_log, int check, int *restore_flag,
@@ -228,7 +228,7 @@ static int chunk_count(const tusq_plan_t *p, const tusq_run_opts *o) {
     if (nsm <= 0) nsm = 148;
     const int L = tile_bits(p->n, o);
     const int V = std::min(o->precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64, L);
-    return auto_subtrees(p->n, o, (uint64_t)nsm * pass_occupancy(o->precision, V, L, false));
+    return auto_subtrees(p->n, o, (uint64_t)nsm * pass_occupancy(o->precision, V, L, 0));
 }
 
 // Device bytes an exec of this plan needs (state + snapshots + program).
@@ -333,13 +333,13 @@ int exec_prepare(const tusq_plan_t *p, const tusq_run_opts *o, tusq_exec **out) 
     e->n_snaps = pg.n_snap_slots;
     // grid of every pass
     e->grid_of_pass.resize(pg.passes.size());
-    int occ_cache[2][16] = {{0}};
+    int occ_cache[4][16] = {{0}};
     for (size_t i = 0; i < pg.passes.size(); ++i) {
         const PassDesc &d = pg.passes[i];
         int V = std::min(e->V, d.L);
-        const bool dense = (d.flags & PF_DENSE) != 0;
-        int &occ = occ_cache[dense ? 1 : 0][d.L];
-        if (!occ) occ = pass_occupancy(o->precision, V, d.L, dense);
+        const int tc = pass_dense_mode(d.flags);
+        int &occ = occ_cache[tc][d.L];
+        if (!occ) occ = pass_occupancy(o->precision, V, d.L, tc);
         uint64_t g = std::min<uint64_t>(d.ntiles, (uint64_t)e->nsm * occ);
         e->grid_of_pass[i] = (int)std::max<uint64_t>(g, 1);
         e->max_grid = std::max(e->max_grid, e->grid_of_pass[i]);

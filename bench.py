@@ -54,9 +54,11 @@ WORKLOAD_DESC = {
     "random_layers_6q": "6-qubit random layers depth 20, depolarizing 1e-3/1e-2, 1e4 shots",
     "qaoa_26q": "26-qubit QAOA on a seeded random 3-regular graph, p=4 layers RZZ(gamma)+RX(beta), "
                 "2q depolarizing 5e-3, 1q 5e-4, 1e6 shots, alpha=0.01 beta=100 (profiling case)",
+    "brickwork_24q": "24-qubit brickwork depth 40, Haar SU(2) + CZ, depolarizing 1e-3/1e-2, 1e6 shots "
+                     "(state above L2)",
 }
 SHOTS = {"qaoa_28q": 1_000_000, "brickwork_20q": 1_000_000, "random_layers_6q": 10_000,
-         "qaoa_26q": 1_000_000}
+         "qaoa_26q": 1_000_000, "brickwork_24q": 1_000_000}
 
 
 def measured_peaks():

@@ -349,4 +349,6 @@ WORKLOADS = {
     "qaoa_28q": lambda: qaoa_3regular(28, 4, 0, 5e-4, 5e-3),
     # same recipe at 26 qubits (512 MiB complex64 state): the profiling case
     "qaoa_26q": lambda: qaoa_3regular(26, 4, 0, 5e-4, 5e-3),
+    # config 2's recipe at 24 qubits (128 MiB complex64 state, above L2)
+    "brickwork_24q": lambda: brickwork(24, 40, 0, 1e-3, 1e-2),
 }

@@ -532,6 +532,14 @@ int tusq_submit(tusq_server *s, const tusq_plan_t *p, const tusq_run_opts *opts,
 /* Non-blocking: *done = 1 once finished (latency_s then set). */
 int tusq_poll(tusq_server *s, uint64_t job_id, int *done, double *latency_s);
 
+/* Where a submitted job is: compiling on the server's host threads, ready
+ * (compiled, waiting for memory, a stream slot or the jobs submitted before
+ * it), running (admitted: its program is on the device and its traversal
+ * queued on its stream) or done.  Non-blocking; TUSQ_ENOTFOUND for an
+ * unknown job id. */
+enum tusq_job_state { TUSQ_JOB_COMPILING = 0, TUSQ_JOB_READY = 1, TUSQ_JOB_RUNNING = 2, TUSQ_JOB_DONE = 3 };
+int tusq_job_state(tusq_server *s, uint64_t job_id, int *state);
+
 /* Device-time interval of a finished job's traversal: the CUDA events
  * recorded on its stream just before its first kernel and just after its
  * last, in ms since the server was created (comparable between jobs, e.g.

@@ -27,6 +27,7 @@ C64, C128 = 0, 1
 COMMUTE_OFF, COMMUTE_PAPER, COMMUTE_CLIFFORD = 0, 1, 2
 DFTT, FROM_SCRATCH, DFTT_SNAPSHOT = 0, 1, 2
 TC_NONE, TC_TF32X3, TC_BF16X3, TC_TF32 = 0, 1, 2, 3
+JOB_COMPILING, JOB_READY, JOB_RUNNING, JOB_DONE = 0, 1, 2, 3
 
 # Every symbol include/tusq.h declares.
 EXPORTS = [
@@ -39,7 +40,7 @@ EXPORTS = [
     "tusq_exec_set_profiling", "tusq_exec_set_dense_skip", "tusq_exec_pass_profile", "tusq_exec_pass_structure", "tusq_exec_free",
     "tusq_run", "tusq_run_noalloc", "tusq_run_streamed", "tusq_dense_check", "tusq_measure_alu_peaks", "tusq_sample", "tusq_batch_create", "tusq_batch_launch", "tusq_batch_finish",
     "tusq_batch_free", "tusq_batch_group_jobs", "tusq_batch_set_stall_test", "tusq_batch_autotune", "tusq_server_create", "tusq_submit", "tusq_poll",
-    "tusq_poll_device_interval", "tusq_server_drain",
+    "tusq_poll_device_interval", "tusq_job_state", "tusq_server_drain",
     "tusq_server_free", "tusq_last_error",
 ]
 
@@ -141,6 +142,7 @@ def _load():
         "tusq_submit": (i32, [vp, vp, P(RunOpts), vp, P(u64)]),
         "tusq_poll": (i32, [vp, u64, P(i32), P(f64)]),
         "tusq_poll_device_interval": (i32, [vp, u64, P(f64), P(f64)]),
+        "tusq_job_state": (i32, [vp, u64, P(i32)]),
         "tusq_server_drain": (i32, [vp]),
         "tusq_server_free": (None, [vp]),
         "tusq_last_error": (ctypes.c_char_p, []),
@@ -539,6 +541,12 @@ class Server:
         lat = ctypes.c_double()
         _check(lib.tusq_poll(self.h, job_id, ctypes.byref(done), ctypes.byref(lat)))
         return bool(done.value), lat.value
+
+    def state(self, job_id: int) -> int:
+        """JOB_COMPILING, JOB_READY, JOB_RUNNING or JOB_DONE."""
+        st = ctypes.c_int()
+        _check(lib.tusq_job_state(self.h, job_id, ctypes.byref(st)))
+        return st.value
 
     def device_interval(self, job_id: int):
         """(start_ms, end_ms) of a finished job's traversal on the device, in ms

@@ -310,6 +310,17 @@ int tusq_poll(tusq_server *s, uint64_t job_id, int *done, double *latency_s) {
     return TUSQ_OK;
 }
 
+int tusq_job_state(tusq_server *s, uint64_t job_id, int *state) {
+    if (!s || !state) { set_error("tusq_job_state: NULL argument"); return TUSQ_EINVAL; }
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) { set_error("tusq_job_state: unknown job id"); return TUSQ_ENOTFOUND; }
+    static_assert(J_COMPILING == TUSQ_JOB_COMPILING && J_READY == TUSQ_JOB_READY &&
+                  J_RUNNING == TUSQ_JOB_RUNNING && J_DONE == TUSQ_JOB_DONE, "job states");
+    *state = it->second.state;
+    return TUSQ_OK;
+}
+
 int tusq_poll_device_interval(tusq_server *s, uint64_t job_id, double *start_ms, double *end_ms) {
     if (!s || !start_ms || !end_ms) { set_error("tusq_poll_device_interval: NULL argument"); return TUSQ_EINVAL; }
     std::lock_guard<std::mutex> g(s->mu);

@@ -48,21 +48,38 @@ def test_admission_refuses_oversize_job():
 
 
 def test_admitted_jobs_overlap_on_the_device():
-    # two jobs admitted together run concurrently: their traversals' device
-    # intervals (CUDA events on their streams) overlap for most of the
-    # shorter one.  16-qubit passes have 8 tiles each, so one job leaves most
-    # of the GPU idle for the other.  The two jobs are the same plan, so that
-    # their compiles (on the server's host threads) end together and neither
-    # waits for the other's to finish.
+    # a job admitted while another runs executes concurrently with it: their
+    # traversals' device intervals (CUDA events on their streams) overlap.
+    # 16-qubit passes have 8 tiles each, so one job leaves most of the GPU
+    # idle for the other.  The short job is submitted once the long one is
+    # running (about 6600 passes, ~0.5 s on the device), so the outcome does
+    # not depend on how fast the host compiles.
+    import time
     import torch
     opts = T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT)
-    plans = [T.plan(W.brickwork(16, 30, 0, 2e-3, 2e-2), 50_000, 0) for _ in range(2)]
-    outs = [torch.empty(1 << 16, dtype=torch.float64, device="cuda") for _ in plans]
+    long_plan = T.plan(W.brickwork(16, 30, 0, 2e-3, 2e-2), 50_000, 0, beta=1000)
+    short_plan = T.plan(W.brickwork(16, 30, 1, 2e-3, 2e-2), 50_000, 1)
+    outs = [torch.empty(1 << 16, dtype=torch.float64, device="cuda") for _ in range(2)]
     srv = T.Server(hbm_budget_bytes=1 << 34, n_streams=2)
-    ids = [srv.submit(p, o.data_ptr(), opts) for p, o in zip(plans, outs)]
+    a = srv.submit(long_plan, outs[0].data_ptr(), opts)
+    seen = set()
+    t0 = time.monotonic()
+    while srv.state(a) != T.JOB_RUNNING:
+        seen.add(srv.state(a))
+        assert srv.state(a) != T.JOB_DONE and time.monotonic() - t0 < 120
+        time.sleep(0.001)
+    assert seen <= {T.JOB_COMPILING, T.JOB_READY}
+    b = srv.submit(short_plan, outs[1].data_ptr(), opts)
     srv.drain()
-    (a0, a1), (b0, b1) = (srv.device_interval(i) for i in ids)
-    assert 0 <= a0 < a1 and 0 <= b0 < b1
+    assert srv.state(a) == T.JOB_DONE and srv.state(b) == T.JOB_DONE
+    with pytest.raises(T.TusqError) as e:
+        srv.state(b + 1000)
+    assert e.value.code == T.TUSQ_ENOTFOUND
+    (a0, a1), (b0, b1) = srv.device_interval(a), srv.device_interval(b)
+    assert 0 <= a0 < a1 and 0 <= b0 < b1 and a0 < b0
     overlap = min(a1, b1) - max(a0, b0)
-    assert overlap > 0.5 * min(a1 - a0, b1 - b0), ((a0, a1), (b0, b1))
-    assert np.array_equal(outs[0].cpu().numpy(), outs[1].cpu().numpy())
+    assert overlap > 0.5 * (b1 - b0), ((a0, a1), (b0, b1))
+    # each job's result is the one it gets alone
+    for pl, o in ((long_plan, outs[0]), (short_plan, outs[1])):
+        alone, _ = T.run_torch(pl, opts)
+        assert np.array_equal(o.cpu().numpy(), alone.cpu().numpy())

@@ -118,3 +118,27 @@ def test_dense_wait_runs_out_and_reports_timeout(brickwork16):
     info = ex.finish()
     assert info["dense_ops"] > 0
     assert abs(float(probs.sum()) - float(opl.weights[-1])) <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def brickwork22():
+    # 22 qubits: 512 tiles per pass for at most 148 x 2 resident CTAs, so most
+    # CTAs run two tiles and a dense op's B prefetch wraps from a tile's last
+    # dense op to the next tile's first.  Three instances of the oracle's plan.
+    circ = W.brickwork(22, 8, 7, 1e-3, 1e-2)
+    opl = oracle.plan(circ, 5_000, 7)
+    inst, w = opl.inst[:3], np.asarray(opl.weights[:3])
+    return circ, inst, w, oracle.run_instances(circ, inst, w)
+
+
+@pytest.mark.parametrize("mode", [T.TC_BF16X3, T.TC_TF32X3])
+def test_engine_dense_stages_several_tiles_per_cta(brickwork22, mode):
+    import torch
+    circ, inst, w, ref = brickwork22
+    pl = T.tusq_plan_from_instances(T.circuit_from(circ), [[tuple(int(v) for v in e) for e in ev] for ev in inst], w)
+    probs, info = T.run_torch(pl, T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT, tc_mode=mode))
+    torch.cuda.synchronize()
+    assert info["dense_ops"] > 0 and info["unrecovered"] == 0
+    d = np.abs(probs.cpu().numpy() - ref)
+    max_abs, tv = ENGINE_BOUND[mode]
+    assert d.max() <= max_abs and d.sum() <= tv, (mode, d.max(), d.sum())

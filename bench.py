@@ -291,7 +291,7 @@ def run_batch(args, T, torch):
     n_inst = sum(p.stats()["n_instances"] for p in plans)
     outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c in jobs]
     stream = torch.cuda.Stream()
-    base = T.run_opts(precision=T.C64)
+    base = T.run_opts(precision=T.C64, tc_mode=args.tc_mode)
     sample = list(range(0, len(jobs), max(1, len(jobs) // 256)))[:256]
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -338,6 +338,7 @@ def run_batch(args, T, torch):
                                f"{args.batch_shots} shots each", "jobs_run": len(jobs),
                    "rejected_over_work_budget": rejected, "max_job_work": args.max_job_work,
                    "max_job_instances": args.max_job_instances,
+                   "tc_mode": ["none", "tf32x3", "bf16x3", "tf32"][args.tc_mode],
                    "one_launch": {"single_cta_jobs": len(small), "group_jobs": b.group_jobs(),
                                   "graph_replay": True},
                    "instances": n_inst,
@@ -345,7 +346,8 @@ def run_batch(args, T, torch):
                                  "group_ctas": best.group_ctas or 16, "ms_on_sample": tune_ms,
                                  "sample_jobs": len(sample), "seconds": tune_s}},
         "plan_seconds": plan_s, "create_seconds": create_s, "error_vs_oracle": errs,
-        "run_info": {k: info[k] for k in ("passes", "gate_apps", "leaf_passes", "restores", "unrecovered")},
+        "run_info": {k: info[k] for k in ("passes", "gate_apps", "leaf_passes", "restores", "unrecovered",
+                                          "dense_ops")},
         "clocks": clk.summary(),
     }
 

@@ -450,7 +450,11 @@ typedef struct tusq_batch tusq_batch;   /* opaque */
  * use_graph != 0 records the launch into a CUDA graph on the first
  * tusq_batch_launch and replays it afterwards (needs a non-default stream).
  * Options as tusq_run (leaf peek is not used: the state never leaves the
- * CTA).  Plans and outputs must stay alive while the batch exists. */
+ * CTA).  tc_mode (complex64) turns the thread-independent register-stage runs
+ * of 13-qubit tiles -- 13-qubit single-CTA jobs and every group job -- into
+ * tensor-core dense ops as in tusq_run; each CTA of the launch then holds 128
+ * TMEM columns, and a tensor-core wait that runs out stops the batch
+ * (TUSQ_ETIMEOUT).  Plans and outputs must stay alive while the batch exists. */
 int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tusq_run_opts *opts,
                       double *const *probs_dev, int use_graph, void *cuda_stream, tusq_batch **out);
 int tusq_batch_launch(tusq_batch *b, void *cuda_stream);

@@ -18,9 +18,9 @@
 
 namespace tusq {
 void compile_program(const tusq_plan_t &P, const CompileOpts &co, Program &prog);
-cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, bool cooperative, cudaStream_t st);
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int tc, int grid, bool cooperative, cudaStream_t st);
 int job_max_qubits_of(int precision);
-int job_occupancy(int precision);
+int job_occupancy(int precision, int tc);
 }  // namespace tusq
 
 using namespace tusq;
@@ -41,6 +41,9 @@ struct tusq_batch {
     double *d_mats = nullptr;
     float *d_matsf = nullptr;
     uint64_t *d_tmask = nullptr, *d_tphi = nullptr;
+    float *d_dpool = nullptr;           // dense ops' B operand parts (tc_mode)
+    int tc_mode = TUSQ_TC_NONE;
+    uint64_t dense_ops = 0;             // dense ops in the jobs' programs
     unsigned char *d_snaps = nullptr;
     double *d_records = nullptr;
     unsigned int *d_next = nullptr;
@@ -82,7 +85,7 @@ int upload(T **dst, const std::vector<T> &v, cudaStream_t st) {
 
 void free_batch_buffers(tusq_batch *b, cudaStream_t st) {
     void *bufs[] = {b->d_jobs, b->d_steps, b->d_passes, b->d_ops, b->d_mats, b->d_matsf, b->d_tmask,
-                    b->d_tphi, b->d_snaps, b->d_records, b->d_next, b->d_counters, b->d_gstate, b->d_gpart,
+                    b->d_tphi, b->d_dpool, b->d_snaps, b->d_records, b->d_next, b->d_counters, b->d_gstate, b->d_gpart,
                     b->d_bars, b->d_assign, b->d_assign_off, b->d_small};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, st);
@@ -110,10 +113,11 @@ int run_once(tusq_batch *b, cudaStream_t st) {
     a.stall_test = b->stall_test;
     a.abort = b->d_bars + b->n_group;
     a.err = b->d_bars + b->n_group + 1;
+    a.dpool = b->d_dpool;
     B_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int), st));
     B_TRY(cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned long long), st));
     B_TRY(cudaMemsetAsync(b->d_bars, 0, sizeof(unsigned int) * (b->n_group + 2), st));
-    B_TRY(launch_jobs(a, b->precision, b->grid, b->n_group > 0, st));
+    B_TRY(launch_jobs(a, b->precision, b->tc_mode, b->grid, b->n_group > 0, st));
     return TUSQ_OK;
 }
 
@@ -142,6 +146,10 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         set_error("tusq_batch_create: group_ctas must be in [0, 16]");
         return TUSQ_EINVAL;
     }
+    if (o.tc_mode < TUSQ_TC_NONE || o.tc_mode > TUSQ_TC_TF32) {
+        set_error("tusq_batch_create: tc_mode must be TUSQ_TC_NONE, _TF32X3, _BF16X3 or _TF32");
+        return TUSQ_EINVAL;
+    }
     const int vbits = o.precision == TUSQ_C128 ? kRegBitsC128 : kRegBitsC64;
     const int nmax = job_max_qubits_of(o.precision);
     for (uint32_t j = 0; j < n_jobs; ++j) {
@@ -164,6 +172,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     }
     b->precision = o.precision;
     b->drift_tol = o.drift_tol;
+    b->tc_mode = o.precision == TUSQ_C64 ? o.tc_mode : TUSQ_TC_NONE;
     b->n_jobs = (int)n_jobs;
     b->use_graph = use_graph != 0;
     const size_t amp = o.precision == TUSQ_C128 ? 16 : 8;
@@ -171,8 +180,10 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     std::vector<PassDesc> passes;
     std::vector<DevOp> ops;
     std::vector<double> mats;
-    std::vector<float> matsf;
+    std::vector<float> matsf, dpool;
     std::vector<uint64_t> tmask, tphi;
+    // dense ops (complex64, tc_mode): the same mode, so one pool entry size
+    const size_t dense_words = o.tc_mode != TUSQ_TC_NONE ? dense_b_words(o.tc_mode) : 1;
     std::vector<size_t> snap_off, rec_off;
     size_t snap_bytes = 0, rec_count = 0;
     // group jobs: their state, partial sums and barrier counter
@@ -196,6 +207,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         const uint64_t budget = o.snapshot_bytes ? o.snapshot_bytes : 8 * state;
         co.snapshots = (co.checks || o.traversal == TUSQ_DFTT_SNAPSHOT) ? (int)std::min<uint64_t>(budget / state, 64) : 0;
         co.cache_states = o.cache_states;
+        co.tc_mode = o.tc_mode;
         return co;
     };
     // the jobs' programs are independent: compile them on all host cores
@@ -233,6 +245,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
         // relocate the job's program into the batch arrays
         const uint32_t pass_base = (uint32_t)passes.size(), op_base = (uint32_t)ops.size();
         const uint32_t mat_base = (uint32_t)(mats.size() / 32), term_base = (uint32_t)tmask.size();
+        const uint32_t dense_base = (uint32_t)(dpool.size() / dense_words);
         JobDesc jd;
         std::memset(&jd, 0, sizeof jd);
         jd.step0 = (uint32_t)steps.size();
@@ -250,10 +263,18 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
             passes.push_back(d);
         }
         for (DevOp d : pg.ops) {
-            d.mat += mat_base;
+            if (d.type == OP_DENSE) {
+                // pool indices: this op's and the next dense op's
+                b->dense_ops++;
+                d.mat += dense_base;
+                d.a += (int32_t)dense_base;
+            } else {
+                d.mat += mat_base;
+            }
             d.term_begin += term_base;
             ops.push_back(d);
         }
+        dpool.insert(dpool.end(), pg.dense_pool.begin(), pg.dense_pool.end());
         mats.insert(mats.end(), pg.mats.begin(), pg.mats.end());
         matsf.insert(matsf.end(), pg.matsf.begin(), pg.matsf.end());
         tmask.insert(tmask.end(), pg.term_mask.begin(), pg.term_mask.end());
@@ -291,7 +312,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     if ((rc = upload(&b->d_steps, steps, st)) || (rc = upload(&b->d_passes, passes, st)) ||
         (rc = upload(&b->d_ops, ops, st)) || (rc = upload(&b->d_mats, mats, st)) ||
         (rc = upload(&b->d_matsf, matsf, st)) || (rc = upload(&b->d_tmask, tmask, st)) ||
-        (rc = upload(&b->d_tphi, tphi, st))) {
+        (rc = upload(&b->d_tphi, tphi, st)) || (rc = upload(&b->d_dpool, dpool, st))) {
         free_batch_buffers(b, st);
         delete b;
         return rc;
@@ -323,7 +344,7 @@ int tusq_batch_create(const tusq_plan_t *const *plans, uint32_t n_jobs, const tu
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // with group jobs every CTA of the grid must be resident at once (a
     // cooperative launch), and the grid is what the host schedules onto
-    const int resident = nsm * job_occupancy(o.precision);
+    const int resident = nsm * job_occupancy(o.precision, b->tc_mode);
     b->grid = b->n_group ? resident : std::max(1, std::min<int>((int)n_jobs, resident));
     // group jobs, most work first, each onto the k CTAs that fall free
     // earliest (greedy list scheduling); every CTA's entries follow this one
@@ -448,9 +469,10 @@ int tusq_batch_finish(tusq_batch *b, tusq_run_info_t *info) {
         double md;
         std::memcpy(&md, &cnt[2], sizeof md);
         info->max_drift = md;
+        info->dense_ops = b->dense_ops;
     }
     if (err) {
-        set_error("tusq_batch_finish: a group barrier's bounded wait ran out; the batch stopped early");
+        set_error("tusq_batch_finish: a bounded wait (group barrier or tensor cores) ran out; the batch stopped early");
         return TUSQ_ETIMEOUT;
     }
     if (cnt[1]) {

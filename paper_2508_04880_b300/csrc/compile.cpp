@@ -13,6 +13,7 @@
 #include <complex>
 #include <cstring>
 #include <stdexcept>
+#include <unordered_map>
 
 #include "internal.h"
 #include "program.h"
@@ -520,6 +521,12 @@ struct Encoder {
     bool lookahead = true;
     bool place_diag = true;     // move diagonal ops to their cheapest register stage
     int tc_mode = TUSQ_TC_NONE;
+    // dense ops' matrices already in the pool: hash of U's bits -> pool
+    // indices, and each entry's unitarity (a traversal re-applies the same
+    // stages for many leaves, so most dense ops repeat an earlier U)
+    std::unordered_map<uint64_t, std::vector<uint32_t>> dense_index;
+    std::vector<uint8_t> dense_unitary;
+    bool keep_dense_u = false;
 
     // Program bytes of one op in shared memory.
     uint32_t op_bytes(const HOp &o) const {
@@ -911,9 +918,28 @@ struct Encoder {
                         d.type = OP_DENSE;
                         d.code = CODE_DENSE;
                         d.sub = (uint32_t)tc_mode;
-                        // b = 1: U is unitary (no Kraus branch in the run), so the
-                        // kernel may restore each vector's norm after the product
+                        // one pool entry per distinct B (the operand the kernel reads;
+                        // U itself in prog.dense_u when kept)
+                        const size_t words = dense_b_words(tc_mode);
+                        std::vector<float> bw(words);
+                        encode_dense_b(o.du.data(), tc_mode, bw.data());
+                        uint64_t h = 1469598103934665603ull;   // FNV-1a over B's bits
                         {
+                            const unsigned char *ub = reinterpret_cast<const unsigned char *>(bw.data());
+                            for (size_t k = 0; k < words * sizeof(float); ++k) h = (h ^ ub[k]) * 1099511628211ull;
+                        }
+                        auto &cands = dense_index[h];
+                        int32_t idx = -1;
+                        for (uint32_t c : cands)
+                            if (std::memcmp(prog.dense_pool.data() + words * c, bw.data(), words * sizeof(float)) == 0) {
+                                idx = (int32_t)c;
+                                break;
+                            }
+                        if (idx < 0) {
+                            idx = (int32_t)dense_unitary.size();
+                            cands.push_back((uint32_t)idx);
+                            // unitary (no Kraus branch in the run): the kernel may
+                            // restore each vector's norm after the product
                             double dev = 0;
                             for (int r = 0; r < 32; ++r)
                                 for (int c2 = 0; c2 < 32; ++c2) {
@@ -921,17 +947,16 @@ struct Encoder {
                                     for (int k = 0; k < 32; ++k) acc += std::conj(o.du[32 * k + r]) * o.du[32 * k + c2];
                                     dev = std::max(dev, std::abs(acc - (r == c2 ? 1.0 : 0.0)));
                                 }
-                            d.b = dev < 1e-9 ? 1 : 0;
+                            dense_unitary.push_back(dev < 1e-9 ? 1 : 0);
+                            if (keep_dense_u)
+                                for (size_t k = 0; k < 1024; ++k) {
+                                    prog.dense_u.push_back(o.du[k].real());
+                                    prog.dense_u.push_back(o.du[k].imag());
+                                }
+                            prog.dense_pool.insert(prog.dense_pool.end(), bw.begin(), bw.end());
                         }
-                        const size_t words = dense_b_words(tc_mode);
-                        d.mat = (uint32_t)(prog.dense_pool.size() / words);
-                        for (size_t k = 0; k < 1024; ++k) {
-                            prog.dense_u.push_back(o.du[k].real());
-                            prog.dense_u.push_back(o.du[k].imag());
-                        }
-                        const size_t at = prog.dense_pool.size();
-                        prog.dense_pool.resize(at + words);
-                        encode_dense_b(o.du.data(), tc_mode, prog.dense_pool.data() + at);
+                        d.mat = (uint32_t)idx;
+                        d.b = dense_unitary[idx];
                         // the absorbed fixed-bit terms: a per-thread constant phase
                         d.phi0 = to_fixed(o.phi0, false);
                         d.term_begin = (uint32_t)prog.term_mask.size();
@@ -1041,6 +1066,7 @@ struct Compiler {
         enc.Lmax = L;
         enc.lookahead = co.schedule == 0;
         enc.tc_mode = co.precision == TUSQ_C64 ? co.tc_mode : TUSQ_TC_NONE;
+        enc.keep_dense_u = co.keep_dense_u;
         // the lowest qubits stay in every window (contiguous 128-byte runs),
         // leaving room for any two-qubit gate
         int nf = std::min(co.precision == TUSQ_C128 ? 3 : 4, std::max(L - 2, 0));

@@ -548,7 +548,6 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
         }
         __syncthreads();
     }
-    if constexpr (TC != 0) dense_teardown(dctx.tmem, tid);
     if (flags & PF_REDUCE) {
         // fixed-order block reduction: warp shuffles, then thread 0
         __shared__ double wsum[3][32];
@@ -567,6 +566,22 @@ __device__ __forceinline__ void pass_body(const PassDesc &d, const void *srcv, v
             partial_out[1] = a1;
             partial_out[2] = a2;
         }
+    }
+}
+
+// The B region is the top of a dense pass's program area (at pbase): the
+// pass's first dense op's B parts are copied there before its first tile,
+// each later op's by the one before (global reads of the pass's ops, so the
+// copy may start before the program is in shared memory).
+__device__ __forceinline__ void dense_pass_prefetch(const PassDesc &d, const DevOp *ops, const float *dpool,
+                                                    unsigned char *pbase, DenseCtx &dc, int tid, int nthr) {
+    for (uint32_t k = 0; k < d.nops; ++k) {
+        const DevOp &op = ops[d.op0 + k];
+        if (op.code != CODE_DENSE) continue;
+        const uint32_t words = dense_b_words_dev(op.sub);
+        dc.bsm = smem_u32(pbase + d.prog_bytes - 4u * words);
+        dense_copy_b(dc.bsm, dpool + (size_t)op.mat * words, 4u * words, tid, nthr);
+        break;
     }
 }
 
@@ -591,16 +606,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
         // dense passes do nothing (the result is void and reported as a timeout)
         if (*args.err) return;
         if (tid == 0) s_abort = 0;
-        // the B region is the top of the program area; the pass's first dense
-        // op's B parts are copied there now, each later op's by the one before
-        const DevOp *gops = args.ops + d.op0;
-        for (uint32_t k = 0; k < d.nops; ++k) {
-            if (gops[k].code != CODE_DENSE) continue;
-            const uint32_t words = dense_b_words_dev(gops[k].sub);
-            dctx.bsm = smem_u32(smem_raw + (sizeof(C2) << d.L) + d.prog_bytes - 4u * words);
-            dense_copy_b(dctx.bsm, args.dpool + (size_t)gops[k].mat * words, 4u * words, tid, blockDim.x);
-            break;
-        }
+        dense_pass_prefetch(d, args.ops, args.dpool, smem_raw + (sizeof(C2) << d.L), dctx, tid, blockDim.x);
         dense_setup(&s_tmem, &s_mbar, tid);
         dctx.tmem = s_tmem;
         dctx.mbar = smem_u32(&s_mbar);
@@ -609,6 +615,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) pass_kernel(const
 
     pass_body<R, V, TC>(d, args.src, args.state, args.snap, args.acc, args.partials + 3 * blockIdx.x, P,
                            smem_raw, blockIdx.x, gridDim.x, dctx, args.dpool);
+    if constexpr (TC != 0) dense_teardown(dctx.tmem, tid);
 }
 
 // state <- |0..0>
@@ -828,9 +835,11 @@ __device__ __forceinline__ bool group_barrier(const BatchArgs &B, unsigned int *
 // a group barrier after each step that writes the state.  Records and drift
 // checks read the members' partial sums after the pass barrier; every member
 // takes the same restore decision, only rank 0 writes records and counters.
-// Returns false when a barrier gave up.
-template <typename R, int V>
-__device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char *smem_raw, unsigned char *pbase) {
+// Returns false when a barrier gave up or a tensor-core wait ran out (TC: the
+// tc mode of the job's dense ops, dc the CTA's tensor-core context).
+template <typename R, int V, int TC>
+__device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char *smem_raw, unsigned char *pbase,
+                              DenseCtx &dc) {
     using C2 = typename C2T<R>::type;
     __shared__ int s_restore;
     const JobDesc &J = B.jobs[j];
@@ -856,11 +865,21 @@ __device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char
         } else if (st.type == ST_PASS) {
             const PassDesc &d = B.passes[st.pass];
             const SProg<R> P = load_program<R>(d, pbase, B.ops, B.mats, B.matsf, B.tmask, B.tphi, tid, nthr);
+            if constexpr (TC != 0)
+                if (d.flags & PF_DENSE) dense_pass_prefetch(d, B.ops, B.dpool, pbase, dc, tid, nthr);
             const void *src = d.src_snap >= 0 ? (const void *)(snaps + dim * d.src_snap) : (const void *)state;
             void *snap = (d.flags & PF_SNAPSHOT) ? (void *)(snaps + dim * d.snap) : nullptr;
-            DenseCtx none{0u, 0u, 0u, nullptr, nullptr, 0};
-            pass_body<R, V, false>(d, src, state, snap, J.acc, J.partials + 3 * rank, P, smem_raw, (uint64_t)rank,
-                                   (uint64_t)k, none);
+            pass_body<R, V, TC>(d, src, state, snap, J.acc, J.partials + 3 * rank, P, smem_raw, (uint64_t)rank,
+                                (uint64_t)k, dc, B.dpool);
+            if constexpr (TC != 0) {
+                // the next pass's program overwrites the B region: the copies
+                // in flight (a prefetch for a next tile) land first
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                if (*dc.abort) {      // uniform: set before a barrier inside the pass
+                    if (tid == 0) atomicExch(B.abort, 1u);
+                    return false;
+                }
+            }
             if (!group_barrier(B, J.bar, width * ++nb, tid)) return false;
         } else if (st.type == ST_RECORD || st.type == ST_CHECK) {
             if (tid == 0) {
@@ -908,8 +927,10 @@ __device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char
 // (register stages on the state held in shared memory), leaf accumulation
 // into the job's FP64 output, snapshot writes and restores, drift records
 // and checks -- without leaving the CTA.  Jobs of uneven size and depth
-// share one launch.
-template <typename R, int V>
+// share one launch.  TC: the tc mode of the batch's tensor-core dense ops
+// (complex64 13-qubit tiles: 13-qubit single-CTA jobs and group jobs); each
+// CTA of such a launch holds 128 TMEM columns from start to end.
+template <typename R, int V, int TC = 0>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const __grid_constant__ BatchArgs B) {
     using C2 = typename C2T<R>::type;
     constexpr bool kC128 = sizeof(R) == 8;
@@ -921,9 +942,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
     __shared__ double s_red[3];
     __shared__ double s_wsum[3][8];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (uint32_t a = B.assign_off[blockIdx.x]; a < B.assign_off[blockIdx.x + 1]; ++a)
-        if (!run_group_job<R, V>(B, (int)B.assign[a].job, (int)B.assign[a].rank, smem_raw, pbase)) return;
-    for (;;) {
+    DenseCtx dctx{0u, 0u, 0u, B.err, nullptr, 0};
+    if constexpr (TC != 0) {
+        __shared__ uint32_t s_tmem;
+        __shared__ __align__(8) uint64_t s_mbar;
+        __shared__ int s_abort;
+        if (tid == 0) s_abort = 0;
+        dense_setup(&s_tmem, &s_mbar, tid);
+        dctx.tmem = s_tmem;
+        dctx.mbar = smem_u32(&s_mbar);
+        dctx.abort = &s_abort;
+    }
+    bool ok = true;
+    for (uint32_t a = B.assign_off[blockIdx.x]; a < B.assign_off[blockIdx.x + 1] && ok; ++a)
+        ok = run_group_job<R, V, TC>(B, (int)B.assign[a].job, (int)B.assign[a].rank, smem_raw, pbase, dctx);
+    while (ok) {
         if (tid == 0) s_job = (int)atomicAdd(B.next_job, 1u);
         __syncthreads();
         const int q = s_job;
@@ -946,8 +979,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
             } else if (st.type == ST_PASS) {
                 const PassDesc &d = B.passes[st.pass];
                 const SProg<R> P = load_program<R>(d, pbase, B.ops, B.mats, B.matsf, B.tmask, B.tphi, tid, nthr);
+                if constexpr (TC != 0)
+                    if (d.flags & PF_DENSE) dense_pass_prefetch(d, B.ops, B.dpool, pbase, dctx, tid, nthr);
                 __syncthreads();
-                run_stages<R, V>(tile, d, P, tid, 0);
+                run_stages<R, V, TC>(tile, d, P, tid, 0, TC != 0 ? &dctx : nullptr, B.dpool);
+                if constexpr (TC != 0) {
+                    // the next pass's program overwrites the B region
+                    asm volatile("cp.async.wait_all;" ::: "memory");
+                    if (*dctx.abort) {    // uniform: set before the last stage barrier
+                        if (tid == 0) atomicExch(B.abort, 1u);
+                        ok = false;
+                        break;
+                    }
+                }
                 const uint32_t flags = d.flags;
                 double rn = 0, rr = 0, ri = 0;
                 C2 *sn = (flags & PF_SNAPSHOT) ? reinterpret_cast<C2 *>(J.snaps) + (size_t)d.snap * N : nullptr;
@@ -1019,12 +1063,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
             }
         }
     }
+    if constexpr (TC != 0) dense_teardown(dctx.tmem, tid);
 }
 
-template <typename R, int V>
+template <typename R, int V, int TC = 0>
 static cudaError_t launch_job_t(const BatchArgs &b, int grid, bool cooperative, cudaStream_t st) {
     const size_t smem = (sizeof(R) * 2 << job_max_qubits<R>()) + kMaxPassProgramBytes;
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<R, V, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // group jobs wait at barriers for CTAs of the same launch: the
     // cooperative attribute guarantees that the whole grid is resident
@@ -1038,40 +1083,47 @@ static cudaError_t launch_job_t(const BatchArgs &b, int grid, bool cooperative, 
     attr[0].val.cooperative = cooperative ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, job_kernel<R, V>, b);
+    e = cudaLaunchKernelEx(&cfg, job_kernel<R, V, TC>, b);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 // One launch over every job of a batch; `grid` CTAs drain the work queue.
-cudaError_t launch_jobs(const BatchArgs &b, int precision, int grid, bool cooperative, cudaStream_t st) {
+// tc: the tc mode of the batch's dense ops (complex64), 0 for none.
+cudaError_t launch_jobs(const BatchArgs &b, int precision, int tc, int grid, bool cooperative, cudaStream_t st) {
     if (precision == TUSQ_C128) return launch_job_t<double, kRegBitsC128>(b, grid, cooperative, st);
-    return launch_job_t<float, kRegBitsC64>(b, grid, cooperative, st);
+    switch (tc) {
+    case TUSQ_TC_TF32X3: return launch_job_t<float, kRegBitsC64, TUSQ_TC_TF32X3>(b, grid, cooperative, st);
+    case TUSQ_TC_BF16X3: return launch_job_t<float, kRegBitsC64, TUSQ_TC_BF16X3>(b, grid, cooperative, st);
+    case TUSQ_TC_TF32: return launch_job_t<float, kRegBitsC64, TUSQ_TC_TF32>(b, grid, cooperative, st);
+    default: return launch_job_t<float, kRegBitsC64>(b, grid, cooperative, st);
+    }
 }
 
 int job_max_qubits_of(int precision) {
     return precision == TUSQ_C128 ? job_max_qubits<double>() : job_max_qubits<float>();
 }
 
-// Resident job CTAs per SM.
-int job_occupancy(int precision) {
+// Resident job CTAs per SM (tc: the instantiation of that tc mode).
+template <typename R, int V, int TC = 0>
+static int job_occupancy_t() {
+    const size_t smem = (sizeof(R) * 2 << job_max_qubits<R>()) + kMaxPassProgramBytes;
     int nb = 0;
-    if (precision == TUSQ_C128) {
-        const size_t smem = (16 << job_max_qubits<double>()) + kMaxPassProgramBytes;
-        if (cudaFuncSetAttribute(job_kernel<double, kRegBitsC128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, job_kernel<double, kRegBitsC128>, 256, smem) !=
-                cudaSuccess)
-            return 1;
-    } else {
-        const size_t smem = (8 << job_max_qubits<float>()) + kMaxPassProgramBytes;
-        if (cudaFuncSetAttribute(job_kernel<float, kRegBitsC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, job_kernel<float, kRegBitsC64>, 256, smem) !=
-                cudaSuccess)
-            return 1;
-    }
+    if (cudaFuncSetAttribute(job_kernel<R, V, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, job_kernel<R, V, TC>, 256, smem) != cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
+}
+
+int job_occupancy(int precision, int tc) {
+    if (precision == TUSQ_C128) return job_occupancy_t<double, kRegBitsC128>();
+    switch (tc) {
+    case TUSQ_TC_TF32X3: return job_occupancy_t<float, kRegBitsC64, TUSQ_TC_TF32X3>();
+    case TUSQ_TC_BF16X3: return job_occupancy_t<float, kRegBitsC64, TUSQ_TC_BF16X3>();
+    case TUSQ_TC_TF32: return job_occupancy_t<float, kRegBitsC64, TUSQ_TC_TF32>();
+    default: return job_occupancy_t<float, kRegBitsC64>();
+    }
 }
 
 }  // namespace tusq

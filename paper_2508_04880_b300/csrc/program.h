@@ -86,7 +86,8 @@ enum DevCode : uint32_t { CODE_MAT1 = 0, CODE_MAT2 = 32, CODE_SWAP = 48, CODE_DI
 // the pool index of the dense op that follows in the pass, cyclically (the
 // first op of the next tile after the last); a == mat: the region already
 // holds it.  Program::dense_u holds U itself (row-major, 2048 doubles from
-// mat * 2048) for host-side interpreters.  phi0 and the
+// mat * 2048) for host-side interpreters, when CompileOpts::keep_dense_u is
+// set.  Dense ops with equal B parts share one pool entry.  phi0 and the
 // csr[0]..csr[1] terms are diagonal terms on fixed bits only: a per-thread
 // constant phase (mu_mask is 0).  b = 1 when U is unitary: each thread's
 // 32-vector then keeps its norm, which the kernel restores after the
@@ -276,8 +277,9 @@ struct BatchArgs {
     const uint32_t *small_ids;
     int32_t n_small;
     int32_t stall_test;              // test hook: group barriers wait for one member too many
-    unsigned int *abort;             // set when a group barrier's bounded wait ran out
+    unsigned int *abort;             // set when a bounded wait ran out (group barrier or tensor cores)
     unsigned int *err;               // bit 0: a bounded wait ran out
+    const float *dpool;              // B operand parts of the jobs' dense ops (relocated pool indices)
 };
 
 // Fuse every unconditional snapshot restore into the pass that follows it
@@ -297,6 +299,7 @@ struct CompileOpts {
     int schedule;          // 0 lookahead window growth, 1 list order
     int cache_states = 0;  // DFTT+Caching capacity; < 0: one per layer, at most kDefaultCacheStates
     int tc_mode = TUSQ_TC_NONE;  // tensor-core dense stages (complex64 only)
+    bool keep_dense_u = false;   // also store each dense op's U in Program::dense_u (host interpreters)
 };
 
 constexpr int kDefaultCacheStates = 8;

@@ -205,6 +205,7 @@ extern "C" int emu_run(const tusq_plan_t *p, const tusq_run_opts *o, double *pro
     co.snapshots = snaps ? (int)std::min<uint64_t>(o->snapshot_bytes / state_bytes, 64) : 0;
     co.cache_states = o->cache_states;
     co.tc_mode = o->tc_mode;
+    co.keep_dense_u = true;     // the interpreter applies each dense op's U
     Program pg;
     compile_program(*p, co, pg);
     const uint64_t dim = 1ULL << p->n;

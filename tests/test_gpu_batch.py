@@ -168,3 +168,36 @@ def test_group_jobs_graph_replay_and_bounded_barrier():
         b.finish()
         for a_, o in zip(first, outs):
             assert np.array_equal(a_, o.cpu().numpy())
+
+
+# tensor-core dense ops in the batch: 13-qubit single-CTA jobs (the whole
+# state is the tile) and group jobs (13-qubit tiles in global memory), held to
+# the split modes' complex64 bound against the oracle
+TC_BOUND = (1e-5, 1e-4)
+
+
+@pytest.fixture(scope="module")
+def tc_refs():
+    jobs = [(W.brickwork(13, 10, 21, 1e-3, 1e-2), 5_000, 21),
+            (W.brickwork(15, 8, 22, 1e-3, 1e-2), 5_000, 22),
+            (W.qaoa_3regular(12, 2, 23, 1e-3, 1e-2), 5_000, 23),
+            (W.brickwork(16, 6, 24, 2e-3, 2e-2), 3_000, 24),
+            (W.brickwork(9, 12, 25, 1e-3, 1e-2), 5_000, 25)]
+    return jobs, [oracle.run(c, s, seed)[0] for c, s, seed in jobs]
+
+
+@pytest.mark.parametrize("mode", [T.TC_BF16X3, T.TC_TF32X3])
+def test_batch_dense_stages_match_oracle(tc_refs, mode):
+    import torch
+    jobs, refs = tc_refs
+    plans = [T.plan(c, s, seed) for c, s, seed in jobs]
+    outs = [torch.empty(1 << c.n_qubits, dtype=torch.float64, device="cuda") for c, _, _ in jobs]
+    b = T.Batch(plans, [o.data_ptr() for o in outs],
+                T.run_opts(precision=T.C64, traversal=T.DFTT_SNAPSHOT, tc_mode=mode))
+    assert b.group_jobs() == 2
+    b.launch()
+    info = b.finish()
+    assert info["dense_ops"] > 0 and info["unrecovered"] == 0
+    for (c, s, seed), o, ref in zip(jobs, outs, refs):
+        d = np.abs(o.cpu().numpy() - ref)
+        assert d.max() <= TC_BOUND[0] and d.sum() <= TC_BOUND[1], (mode, c.name, d.max(), d.sum())

@@ -920,7 +920,7 @@ __device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char
     return true;
 }
 
-// job_kernel: the persistent launch of a batch.  First each CTA runs its
+// job_body: one CTA's part of a batch launch.  First the CTA runs its
 // share of the group jobs (more amplitudes than one CTA's shared memory
 // holds) in the order the host assigned; then it takes single-CTA jobs from
 // a work queue and runs each job's whole program -- resets, fused passes
@@ -930,8 +930,8 @@ __device__ bool run_group_job(const BatchArgs &B, int j, int rank, unsigned char
 // share one launch.  TC: the tc mode of the batch's tensor-core dense ops
 // (complex64 13-qubit tiles: 13-qubit single-CTA jobs and group jobs); each
 // CTA of such a launch holds 128 TMEM columns from start to end.
-template <typename R, int V, int TC = 0>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const __grid_constant__ BatchArgs B) {
+template <typename R, int V, int TC>
+__device__ __forceinline__ void job_body(const BatchArgs &B, DenseCtx &dctx) {
     using C2 = typename C2T<R>::type;
     constexpr bool kC128 = sizeof(R) == 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -942,21 +942,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
     __shared__ double s_red[3];
     __shared__ double s_wsum[3][8];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    DenseCtx dctx{0u, 0u, 0u, B.err, nullptr, 0};
-    if constexpr (TC != 0) {
-        __shared__ uint32_t s_tmem;
-        __shared__ __align__(8) uint64_t s_mbar;
-        __shared__ int s_abort;
-        if (tid == 0) s_abort = 0;
-        dense_setup(&s_tmem, &s_mbar, tid);
-        dctx.tmem = s_tmem;
-        dctx.mbar = smem_u32(&s_mbar);
-        dctx.abort = &s_abort;
-    }
-    bool ok = true;
-    for (uint32_t a = B.assign_off[blockIdx.x]; a < B.assign_off[blockIdx.x + 1] && ok; ++a)
-        ok = run_group_job<R, V, TC>(B, (int)B.assign[a].job, (int)B.assign[a].rank, smem_raw, pbase, dctx);
-    while (ok) {
+    for (uint32_t a = B.assign_off[blockIdx.x]; a < B.assign_off[blockIdx.x + 1]; ++a)
+        if (!run_group_job<R, V, TC>(B, (int)B.assign[a].job, (int)B.assign[a].rank, smem_raw, pbase, dctx)) return;
+    for (;;) {
         if (tid == 0) s_job = (int)atomicAdd(B.next_job, 1u);
         __syncthreads();
         const int q = s_job;
@@ -988,8 +976,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
                     asm volatile("cp.async.wait_all;" ::: "memory");
                     if (*dctx.abort) {    // uniform: set before the last stage barrier
                         if (tid == 0) atomicExch(B.abort, 1u);
-                        ok = false;
-                        break;
+                        return;
                     }
                 }
                 const uint32_t flags = d.flags;
@@ -1063,7 +1050,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const 
             }
         }
     }
-    if constexpr (TC != 0) dense_teardown(dctx.tmem, tid);
+}
+
+// The persistent launch of a batch: job_body, with (TC) the CTA's 128 TMEM
+// columns allocated before it and freed after it, whichever way it ends.
+template <typename R, int V, int TC = 0>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) job_kernel(const __grid_constant__ BatchArgs B) {
+    DenseCtx dctx{0u, 0u, 0u, B.err, nullptr, 0};
+    if constexpr (TC != 0) {
+        __shared__ uint32_t s_tmem;
+        __shared__ __align__(8) uint64_t s_mbar;
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = 0;
+        dense_setup(&s_tmem, &s_mbar, threadIdx.x);
+        dctx.tmem = s_tmem;
+        dctx.mbar = smem_u32(&s_mbar);
+        dctx.abort = &s_abort;
+    }
+    job_body<R, V, TC>(B, dctx);
+    if constexpr (TC != 0) dense_teardown(dctx.tmem, threadIdx.x);
 }
 
 template <typename R, int V, int TC = 0>

@@ -137,3 +137,16 @@ def test_library_loads_and_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert sorted(T.EXPORTS) == names
+
+
+def test_host_side_option_checks():
+    # checks that run before any CUDA call: a batch's tc_mode out of range,
+    # and the serving loop's job-state query without a server
+    pl = T.plan(W.brickwork(6, 2, 0, 1e-3, 1e-2), 100, 0)
+    for bad in (-1, 4):
+        with pytest.raises(T.TusqError) as e:
+            T.Batch([pl], [0x1000], T.run_opts(precision=T.C64, tc_mode=bad))
+        assert e.value.code == T.TUSQ_EINVAL
+    st = ctypes.c_int(-1)
+    assert T.lib.tusq_job_state(None, 1, ctypes.byref(st)) == T.TUSQ_EINVAL
+    assert st.value == -1

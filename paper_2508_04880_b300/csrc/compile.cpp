@@ -581,34 +581,54 @@ struct Encoder {
             d.uid = run.front().uid;
             d.du.assign(32 * 32, cd(0, 0));
             for (int i = 0; i < 32; ++i) d.du[33 * i] = 1.0;
-            std::vector<cd> nu(32 * 32);
+            // unitary unless a Kraus branch (RESET / MEASURE) is in the run
+            d.noninv = false;
+            for (const HOp &o : run) d.noninv = d.noninv || o.noninv;
+            // U <- M_o U for each op in order, applied by its structure: a 2x2
+            // mixes row pairs, a 4x4 row quads, a diagonal scales rows (each
+            // new entry sums the same products in the same order as the full
+            // 32x32 product would)
             for (const HOp &o : run) {
                 if (&o != &run.front()) {
                     d.merged.push_back(o.uid);
                 }
                 d.merged.insert(d.merged.end(), o.merged.begin(), o.merged.end());
-                // M_o (32x32 in the register basis), then U <- M_o U
-                std::vector<cd> m(32 * 32, cd(0, 0));
+                std::vector<cd> &u = d.du;
                 if (o.type == H_MAT1) {
                     const int b = regidx[local[o.q0]];
                     for (int r = 0; r < 32; ++r) {
                         if (r >> b & 1) continue;
                         const int r1 = r | 1 << b;
-                        m[32 * r + r] = o.m[0];
-                        m[32 * r + r1] = o.m[1];
-                        m[32 * r1 + r] = o.m[2];
-                        m[32 * r1 + r1] = o.m[3];
+                        for (int c = 0; c < 32; ++c) {
+                            const cd x = u[32 * r + c], y = u[32 * r1 + c];
+                            u[32 * r + c] = o.m[0] * x + o.m[1] * y;
+                            u[32 * r1 + c] = o.m[2] * x + o.m[3] * y;
+                        }
                     }
                 } else if (o.type == H_MAT2) {
                     const int ra = regidx[local[o.q0]], rb = regidx[local[o.q1]];
-                    for (int r = 0; r < 32; ++r)
+                    const int both = (1 << ra) | (1 << rb);
+                    for (int base = 0; base < 32; ++base) {
+                        if (base & both) continue;
+                        // the quad's rows in ascending order, with their 4x4 indices
+                        int rows[4], li[4];
+                        int nq = 0;
+                        for (int r = base; r < 32; ++r)
+                            if ((r & ~both) == base) {
+                                rows[nq] = r;
+                                li[nq] = 2 * (r >> ra & 1) + (r >> rb & 1);
+                                ++nq;
+                            }
                         for (int c = 0; c < 32; ++c) {
-                            const int outside = ~((1 << ra) | (1 << rb)) & 31;
-                            if ((r & outside) != (c & outside)) continue;
-                            const int lr = 2 * (r >> ra & 1) + (r >> rb & 1);
-                            const int lc = 2 * (c >> ra & 1) + (c >> rb & 1);
-                            m[32 * r + c] = o.m[4 * lr + lc];
+                            cd x[4];
+                            for (int q = 0; q < 4; ++q) x[q] = u[32 * rows[q] + c];
+                            for (int q = 0; q < 4; ++q) {
+                                cd acc = 0;
+                                for (int k = 0; k < 4; ++k) acc += o.m[4 * li[q] + li[k]] * x[k];
+                                u[32 * rows[q] + c] = acc;
+                            }
                         }
+                    }
                 } else {
                     // register-only terms into the matrix; fixed-only ones ride along
                     d.phi0 += o.phi0;
@@ -621,18 +641,12 @@ struct Encoder {
                                 if (t.first & greg[i]) mu |= 1 << i;
                             if (__builtin_popcount(r & mu) & 1) turns += t.second;
                         }
-                        m[32 * r + r] = std::polar(1.0, 2 * kPi * turns);
+                        const cd ph = std::polar(1.0, 2 * kPi * turns);
+                        for (int c = 0; c < 32; ++c) u[32 * r + c] = ph * u[32 * r + c];
                     }
                     for (auto &t : o.terms)
                         if ((t.first & rg) == 0) d.terms.push_back(t);
                 }
-                for (int r = 0; r < 32; ++r)
-                    for (int c = 0; c < 32; ++c) {
-                        cd acc = 0;
-                        for (int k = 0; k < 32; ++k) acc += m[32 * r + k] * d.du[32 * k + c];
-                        nu[32 * r + c] = acc;
-                    }
-                d.du.swap(nu);
             }
             out.push_back(d);
             run.clear();
@@ -940,14 +954,7 @@ struct Encoder {
                             cands.push_back((uint32_t)idx);
                             // unitary (no Kraus branch in the run): the kernel may
                             // restore each vector's norm after the product
-                            double dev = 0;
-                            for (int r = 0; r < 32; ++r)
-                                for (int c2 = 0; c2 < 32; ++c2) {
-                                    cd acc = 0;
-                                    for (int k = 0; k < 32; ++k) acc += std::conj(o.du[32 * k + r]) * o.du[32 * k + c2];
-                                    dev = std::max(dev, std::abs(acc - (r == c2 ? 1.0 : 0.0)));
-                                }
-                            dense_unitary.push_back(dev < 1e-9 ? 1 : 0);
+                            dense_unitary.push_back(o.noninv ? 0 : 1);
                             if (keep_dense_u)
                                 for (size_t k = 0; k < 1024; ++k) {
                                     prog.dense_u.push_back(o.du[k].real());
